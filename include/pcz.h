@@ -1,0 +1,165 @@
+/*
+ * pcz.h -- C ABI of libpcz: GPU multi-component progressive-precision
+ * compression and retrieval of floating-point fields, after Magri & Lindstrom,
+ * "A General Framework for Progressive Data Compression and Retrieval".
+ *
+ * A field x is stored as n components.  Component i is an error-bounded lossy
+ * compression y_i = C(e, tau_i) of the residual e = x - x~_{i-1} left by the
+ * components before it, and x~_i = x~_{i-1} + D(y_i) (Algorithm 1, Sec. 4.1).
+ * Reading the first k components back and summing them left to right gives x~_k
+ * (Algorithm 2, Sec. 4.2), with ||x - x~_k||_inf <= tau_k (Eq. 1, Sec. 4.3).
+ * The compressor C/D is a zfp-style coder of 4^d-value blocks ("bricks") with
+ * one exponent per block and component (Sec. 4.4) and group-tested bit planes
+ * (Sec. 2).
+ *
+ * Conventions shared by every call:
+ *  - Fields are dense, x fastest: element (ix, iy, iz) sits at
+ *    ix + dims[0] * (iy + dims[1] * iz).  ndims is 1, 2 or 3; extents need not
+ *    be multiples of 4.
+ *  - Device pointers are CUDA global memory on the current device; host
+ *    pointers are accepted where stated and are copied through the same stream.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    are asynchronous on it except where they must read a result back.
+ *  - The caller owns its input and output buffers.  The library owns the
+ *    component streams (device memory) until pc_streams_free.
+ *  - No C++ exception crosses this interface.  Every call returns a pc_status;
+ *    pc_last_error() gives a message for the last failure on this thread.
+ *  - Not thread-safe on one pc_streams object; different objects may be used
+ *    from different threads.
+ */
+#ifndef PCZ_H
+#define PCZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PC_MAX_COMPONENTS 64
+
+typedef enum { PC_F32 = 1, PC_F64 = 2 } pc_dtype;
+
+typedef enum {
+  PC_OK = 0,
+  PC_ERR_ARG = 1,              /* a pointer, size, extent or index is invalid */
+  PC_ERR_TAU_ORDER = 2,        /* tolerances not finite, positive and strictly decreasing */
+  PC_ERR_NONFINITE = 3,        /* the field holds a NaN or an infinity */
+  PC_ERR_OOM = 4,              /* a device allocation failed */
+  PC_ERR_CUDA = 5,             /* a CUDA call failed; see pc_last_error() */
+  PC_ERR_CORRUPT_STREAM = 6,   /* a component stream does not parse */
+  PC_ERR_TOL_UNREACHABLE = 7,  /* tolerance finer than the last component's */
+  PC_ERR_VERSION = 8           /* serialized data of another format or version */
+} pc_status;
+
+typedef struct pc_streams pc_streams; /* opaque */
+
+/* Half-open box [lo, hi) in element units, lo[a] < hi[a] <= dims[a]; entries
+ * beyond ndims are ignored.  A NULL box means the whole field. */
+typedef struct {
+  int64_t lo[3], hi[3];
+} pc_box;
+
+/*
+ * Algorithm 1 (Sec. 4.1): compresses the field into n components with
+ * tolerances tau[0] > tau[1] > ... > tau[n-1] > 0 (absolute, max-norm).
+ *   field   device or host pointer to prod(dims) values of dtype.
+ *   dims    ndims extents, dims[0] fastest.
+ *   tau     host array of n doubles; n in 1..PC_MAX_COMPONENTS.
+ *   out     receives a new pc_streams (free with pc_streams_free).
+ * The field must be finite (Sec. 6.1: NaN, infinities and signed zeros are not
+ * handled); otherwise PC_ERR_NONFINITE and *out is left NULL.  Synchronises
+ * once on cuda_stream to read the component sizes back.
+ */
+pc_status pc_compress(const void *field, const int64_t *dims, int ndims, pc_dtype dtype, const double *tau,
+                      int n, void *cuda_stream, pc_streams **out);
+
+/*
+ * Tolerance query (Sec. 6.2, "Benefits"): the number of components k that a
+ * request at tolerance tau needs, k = min{i : tau_i <= tau} (1-based); a tau at
+ * or above tau_1 gives 1.  PC_ERR_TOL_UNREACHABLE when tau < tau_n.
+ */
+pc_status pc_query_k(const pc_streams *s, double tau, int *k_out);
+
+/*
+ * Algorithm 2 (Sec. 4.2): x~_k = fl(...fl(fl(0 + D(y_1)) + D(y_2))... + D(y_k)),
+ * written for the box into out (device or host pointer to the box's values,
+ * x fastest, dtype of the field).  If tau >= 0, k is taken from pc_query_k(tau)
+ * and the k argument is ignored; if tau < 0, k (0..n) is used as given (k = 0
+ * writes zeros).  Only bricks that meet the box are decoded (Sec. 6.1: single
+ * 4^d blocks can be decoded on their own).
+ */
+pc_status pc_retrieve(const pc_streams *s, double tau, int k, const pc_box *box, void *out, void *cuda_stream);
+
+/*
+ * Incremental refinement (Sec. 4.2: the reconstruction is refined by further
+ * loop iterations of Algorithm 2): inout holds x~_k0 on the box (as written by
+ * pc_retrieve or pc_refine with k0 components) and receives x~_k, 0 <= k0 <= k
+ * <= n.  The result is bit-identical to pc_retrieve with k components.
+ * inout is a device or host pointer.
+ */
+pc_status pc_refine(const pc_streams *s, int k0, int k, const pc_box *box, void *inout, void *cuda_stream);
+
+/*
+ * Per-component metadata (the tolerance stored as metadata, Sec. 6.2) and size:
+ * component i (0-based) has tolerance *tau_i, a payload of *bits bits (chunk
+ * padding included) and an index of *index_bytes bytes.  Any output may be NULL.
+ */
+pc_status pc_stream_info(const pc_streams *s, int i, double *tau_i, uint64_t *bits, uint64_t *index_bytes);
+
+/*
+ * Field shape and component count of a pc_streams.  dims receives 3 extents
+ * (1 beyond ndims).  Any output may be NULL.
+ */
+pc_status pc_streams_shape(const pc_streams *s, int *ndims, int64_t *dims, pc_dtype *dtype, int *n);
+
+/*
+ * Block-mode counters of component i (0-based) from pc_compress: counts[0] =
+ * bricks coded ZERO, [1] = CODED, [2] = RAW, [3] = total escalation steps,
+ * [4] = field values where Eq. 1 failed in floating point (Sec. 4.3).
+ */
+pc_status pc_stream_counts(const pc_streams *s, int i, uint64_t counts[5]);
+
+/*
+ * Serialization (checkpoint/restart use, Sec. 5.1.1): writes the header, the
+ * tolerances and every component's index and payload into h_buf (host memory,
+ * *len bytes).  With h_buf NULL only *len is set to the size needed.
+ * Synchronises cuda_stream.
+ */
+pc_status pc_streams_serialize(const pc_streams *s, void *h_buf, size_t *len, void *cuda_stream);
+
+/* Inverse of pc_streams_serialize: the data (host memory) is checked and copied
+ * to the device.  PC_ERR_VERSION for another format, PC_ERR_CORRUPT_STREAM for
+ * inconsistent sizes. */
+pc_status pc_streams_deserialize(const void *h_buf, size_t len, void *cuda_stream, pc_streams **out);
+
+/* Device pointers of component i's data (for users that move components
+ * between memories themselves, Sec. 6.2): payload (u64 words), chunk word
+ * offsets (u64 per 32 bricks) and brick bit lengths (u16 per brick). */
+pc_status pc_stream_device_ptrs(const pc_streams *s, int i, const uint64_t **payload, const uint64_t **chunk_word,
+                                const uint16_t **brick_len, uint64_t *payload_words, uint64_t *nchunks,
+                                uint64_t *nbricks);
+
+/* Releases the streams and their device memory (waits for the device). */
+void pc_streams_free(pc_streams *s);
+
+/*
+ * The range min/max of a device field (Sec. 5.1: tau_0 is the range of the
+ * field values), reduced on cuda_stream; *vmin and *vmax receive the extreme
+ * values as doubles.  Synchronises.  PC_ERR_NONFINITE if a value is not finite.
+ */
+pc_status pc_field_range(const void *d_field, int64_t count, pc_dtype dtype, void *cuda_stream, double *vmin,
+                         double *vmax);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *pc_last_error(void);
+
+/* Library format version (of serialized streams) and build information. */
+int pc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCZ_H */

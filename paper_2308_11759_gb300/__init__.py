@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) implementation of the multi-component progressive-precision
+method of Magri & Lindstrom, "A General Framework for Progressive Data
+Compression and Retrieval" (Sec. 4, Algorithms 1 and 2).
+
+This module is a thin ctypes binding over libpcz.so (include/pcz.h): it only
+marshals arguments (tensor data pointers, shapes, the current CUDA stream).
+Every step of compression and retrieval runs in the library's CUDA kernels;
+there is no CPU fallback, and importing a function that needs the library
+raises if libpcz.so has not been built.
+
+Arrays use C order with shape (nz, ny, nx) for 3D (x fastest); boxes are
+given as (lo, hi) in the same axis order, half-open.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libpcz.so")
+
+PC_F32, PC_F64 = 1, 2
+STATUS = {
+    0: "PC_OK", 1: "PC_ERR_ARG", 2: "PC_ERR_TAU_ORDER", 3: "PC_ERR_NONFINITE", 4: "PC_ERR_OOM",
+    5: "PC_ERR_CUDA", 6: "PC_ERR_CORRUPT_STREAM", 7: "PC_ERR_TOL_UNREACHABLE", 8: "PC_ERR_VERSION",
+}
+
+
+class PczError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Box(C.Structure):
+    _fields_ = [("lo", C.c_int64 * 3), ("hi", C.c_int64 * 3)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libpcz.so (raises if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise ImportError(f"{LIBPATH} is not built; run __graft_entry__.build() (there is no CPU fallback)")
+        L = C.CDLL(LIBPATH)
+        vp, i64p, dp, ip = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int)
+        u64p = C.POINTER(C.c_uint64)
+        sig = {
+            "pc_compress": [vp, i64p, C.c_int, C.c_int, dp, C.c_int, vp, C.POINTER(vp)],
+            "pc_query_k": [vp, C.c_double, ip],
+            "pc_retrieve": [vp, C.c_double, C.c_int, C.POINTER(Box), vp, vp],
+            "pc_refine": [vp, C.c_int, C.c_int, C.POINTER(Box), vp, vp],
+            "pc_stream_info": [vp, C.c_int, dp, u64p, u64p],
+            "pc_streams_shape": [vp, ip, i64p, ip, ip],
+            "pc_stream_counts": [vp, C.c_int, u64p],
+            "pc_streams_serialize": [vp, vp, C.POINTER(C.c_size_t), vp],
+            "pc_streams_deserialize": [vp, C.c_size_t, vp, C.POINTER(vp)],
+            "pc_stream_device_ptrs": [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), u64p, u64p, u64p],
+            "pc_field_range": [vp, C.c_int64, C.c_int, vp, dp, dp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.pc_streams_free.argtypes = [vp]
+        L.pc_streams_free.restype = None
+        L.pc_last_error.argtypes = []
+        L.pc_last_error.restype = C.c_char_p
+        L.pc_version.argtypes = []
+        L.pc_version.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise PczError(status, lib().pc_last_error().decode())
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _dtype_code(dt) -> int:
+    torch = _torch()
+    if dt in (torch.float32, np.float32) or str(dt) in ("float32", "torch.float32"):
+        return PC_F32
+    if dt in (torch.float64, np.float64) or str(dt) in ("float64", "torch.float64"):
+        return PC_F64
+    raise TypeError(f"unsupported dtype {dt}")
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _box(box, shape):
+    if box is None:
+        return None, tuple(shape)
+    lo, hi = [int(v) for v in box[0]], [int(v) for v in box[1]]
+    nd = len(shape)
+    if len(lo) != nd or len(hi) != nd:
+        raise ValueError("box rank differs from the field's")
+    b = Box()
+    for a in range(3):
+        b.lo[a] = lo[nd - 1 - a] if a < nd else 0
+        b.hi[a] = hi[nd - 1 - a] if a < nd else 1
+    return b, tuple(h - l for l, h in zip(lo, hi))
+
+
+def _ptr(x):
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    raise TypeError("expected a torch tensor or a numpy array")
+
+
+class Streams:
+    """The n compressed components of one field (Algorithm 1's output)."""
+
+    def __init__(self, handle, shape, dtype):
+        self._h = handle
+        self.shape = tuple(shape)
+        self.dtype = dtype
+        n = C.c_int()
+        _check(lib().pc_streams_shape(self._h, None, None, None, C.byref(n)))
+        self.n = n.value
+
+    # ---- construction ---------------------------------------------------
+    @classmethod
+    def compress(cls, x, tau, stream=None):
+        """Algorithm 1 on x (CUDA tensor, or host tensor/array copied in by the
+        library) with tolerances tau (strictly decreasing, > 0)."""
+        torch = _torch()
+        shape = tuple(x.shape)
+        dims = (C.c_int64 * 3)(*([int(s) for s in shape[::-1]] + [1] * (3 - len(shape))))
+        taus = (C.c_double * len(tau))(*[float(t) for t in tau])
+        h = C.c_void_p()
+        dt = x.dtype if isinstance(x, torch.Tensor) else x.dtype.type
+        _check(lib().pc_compress(_ptr(x), dims, len(shape), _dtype_code(dt), taus, len(tau), _stream_ptr(stream),
+                                 C.byref(h)))
+        tdt = x.dtype if isinstance(x, torch.Tensor) else (torch.float32 if x.dtype == np.float32 else torch.float64)
+        return cls(h, shape, tdt)
+
+    @classmethod
+    def deserialize(cls, data: bytes, stream=None):
+        torch = _torch()
+        buf = C.create_string_buffer(bytes(data), len(data))
+        h = C.c_void_p()
+        _check(lib().pc_streams_deserialize(buf, len(data), _stream_ptr(stream), C.byref(h)))
+        nd = C.c_int()
+        dims = (C.c_int64 * 3)()
+        dt = C.c_int()
+        _check(lib().pc_streams_shape(h, C.byref(nd), dims, C.byref(dt), None))
+        shape = tuple(int(dims[a]) for a in range(nd.value))[::-1]
+        return cls(h, shape, torch.float32 if dt.value == PC_F32 else torch.float64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pc_streams_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- queries --------------------------------------------------------
+    def query_k(self, tau: float) -> int:
+        k = C.c_int()
+        _check(lib().pc_query_k(self._h, float(tau), C.byref(k)))
+        return k.value
+
+    def tau(self, i: int) -> float:
+        t = C.c_double()
+        _check(lib().pc_stream_info(self._h, i, C.byref(t), None, None))
+        return t.value
+
+    def info(self, i: int):
+        t, bits, idx = C.c_double(), C.c_uint64(), C.c_uint64()
+        _check(lib().pc_stream_info(self._h, i, C.byref(t), C.byref(bits), C.byref(idx)))
+        return t.value, bits.value, idx.value
+
+    def counts(self, i: int):
+        out = (C.c_uint64 * 5)()
+        _check(lib().pc_stream_counts(self._h, i, out))
+        return [int(v) for v in out]
+
+    def device_ptrs(self, i: int):
+        pl, cw, bl = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        nw, nc, nb = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib().pc_stream_device_ptrs(self._h, i, C.byref(pl), C.byref(cw), C.byref(bl), C.byref(nw),
+                                           C.byref(nc), C.byref(nb)))
+        return pl.value, cw.value, bl.value, nw.value, nc.value, nb.value
+
+    # ---- reconstruction -------------------------------------------------
+    def retrieve(self, k=None, tau=None, box=None, out=None, stream=None):
+        """Algorithm 2: x~_k on the box (k given, or the smallest k meeting tau).
+        Writes into out (device or host tensor/array) or a new CUDA tensor."""
+        torch = _torch()
+        b, ext = _box(box, self.shape)
+        if out is None:
+            out = torch.empty(ext, dtype=self.dtype, device="cuda")
+        t = -1.0 if tau is None else float(tau)
+        kk = 0 if k is None else int(k)
+        if tau is None and k is None:
+            raise ValueError("give k or tau")
+        _check(lib().pc_retrieve(self._h, t, kk, C.byref(b) if b is not None else None, _ptr(out),
+                                 _stream_ptr(stream)))
+        return out
+
+    def refine(self, k0: int, k: int, inout, box=None, stream=None):
+        """Adds components k0+1..k into inout, which holds x~_k0 on the box."""
+        b, _ = _box(box, self.shape)
+        _check(lib().pc_refine(self._h, int(k0), int(k), C.byref(b) if b is not None else None, _ptr(inout),
+                               _stream_ptr(stream)))
+        return inout
+
+    def serialize(self, stream=None) -> bytes:
+        n = C.c_size_t()
+        _check(lib().pc_streams_serialize(self._h, None, C.byref(n), _stream_ptr(stream)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().pc_streams_serialize(self._h, buf, C.byref(n), _stream_ptr(stream)))
+        return buf.raw[: n.value]
+
+
+def compress(x, tau, stream=None) -> Streams:
+    return Streams.compress(x, tau, stream)
+
+
+def field_range(x, stream=None):
+    """(min, max) of a CUDA tensor, reduced on the device."""
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib().pc_field_range(_ptr(x), x.numel(), _dtype_code(x.dtype), _stream_ptr(stream), C.byref(lo),
+                                C.byref(hi)))
+    return lo.value, hi.value
+
+
+# ---- tolerance schedules (Sec. 5.1: tau_i = 2^(-delta i) tau_0, tau_0 = range) ----
+
+def value_range(x, stream=None) -> float:
+    lo, hi = field_range(x, stream)
+    return hi - lo
+
+
+def tau_binary(rng: float, delta: int, n: int):
+    """tau_i = 2^(-delta * i) * tau_0 for i = 1..n."""
+    return [rng * 2.0 ** (-delta * i) for i in range(1, n + 1)]
+
+
+def tau_decade(rng: float, n: int, first_exp: int = 2):
+    """tau_i = 10^-(first_exp + i - 1) * tau_0 for i = 1..n: each decimal factor
+    is the double nearest to it, times the range with one rounding."""
+    return [float("1e-%d" % (first_exp + i - 1)) * rng for i in range(1, n + 1)]

@@ -1,0 +1,73 @@
+"""Builds libpcz.so (the CUDA library behind include/pcz.h) in this directory.
+
+nvcc compiles every translation unit for sm_103a (GB300) in parallel and links
+them into one shared library with the CUDA runtime linked statically.  No
+floating-point contraction, no flush-to-zero, IEEE division and square root.
+"""
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "libpcz.so")
+SOURCES = ["pcz_api.cu", "pcz_compress.cu", "pcz_retrieve.cu", "pcz_misc.cu"]
+HEADERS = ["pcz_device.cuh", "pcz_kernels.h", os.path.join("..", "..", "include", "pcz.h")]
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-fmad=false", "-ftz=false",
+         "-prec-div=true", "-prec-sqrt=true"]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.abspath(__file__)]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and not _stale():
+        return LIB
+    nvcc = _nvcc()
+    with tempfile.TemporaryDirectory(prefix="pcz_build_") as tmp:
+        procs = []
+        objs = []
+        for src in SOURCES:
+            obj = os.path.join(tmp, src.replace(".cu", ".o"))
+            objs.append(obj)
+            cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+        errors = []
+        for src, pr in procs:
+            out, _ = pr.communicate()
+            if verbose and out:
+                print(out)
+            if pr.returncode != 0:
+                errors.append(f"{src}:\n{out}")
+        if errors:
+            raise RuntimeError("libpcz build failed:\n" + "\n".join(errors))
+        tmp_lib = os.path.join(tmp, "libpcz.so")
+        link = [nvcc, *ARCH, "-shared", "-o", tmp_lib, *objs, "-cudart", "static"]
+        r = subprocess.run(link, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("libpcz link failed:\n" + r.stdout + r.stderr)
+        shutil.copy2(tmp_lib, LIB + ".tmp")
+        os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

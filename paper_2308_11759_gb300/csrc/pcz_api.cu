@@ -1,0 +1,686 @@
+// pcz_api.cu -- host side of the C ABI declared in include/pcz.h: argument
+// checks, the scratch pool, kernel launches on the caller's stream, the
+// component streams object and its serialized form.
+//
+// Every step of the method runs in the kernels (pcz_compress.cu,
+// pcz_retrieve.cu, pcz_misc.cu); this file only moves sizes, pointers and
+// per-component metadata (tolerances, Sec. 6.2) around them.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pcz.h"
+#include "pcz_kernels.h"
+
+using namespace pcz;
+
+namespace {
+
+thread_local std::string g_err;
+
+pc_status fail(pc_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+pc_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error so later calls can proceed
+  return fail(e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+  } while (0)
+
+constexpr uint32_t kMagic = 0x315a4350u;  // "PCZ1"
+constexpr uint32_t kFormatVersion = 1;
+
+size_t dsize(pc_dtype t) { return t == PC_F32 ? 4 : 8; }
+
+// Scratch pool per device, grown on demand and kept for later calls.
+struct DevCtx {
+  uint64_t* pool = nullptr;
+  uint64_t pool_words = 0;
+  bool pool_cfg = false;
+};
+std::mutex g_mu;
+DevCtx g_ctx[128];
+
+// Stream-ordered device allocation; freed on the same stream.
+struct Scratch {
+  std::vector<void*> ptrs;
+  cudaStream_t s;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t get(void** p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+// Where a caller's pointer lives.
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// floor(log2 tau) from the bit pattern of a positive finite double.
+int floor_log2_bits(double tau) {
+  uint64_t b;
+  std::memcpy(&b, &tau, 8);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if (be) return be - 1023;
+  const uint64_t f = b & ((1ull << 52) - 1);
+  int hb = 63;
+  while (!((f >> hb) & 1ull)) --hb;
+  return hb - 1074;
+}
+
+// Bit pattern of the largest T value not above tau (so |e| <= tau is an
+// exact comparison of bit patterns on the device).
+uint64_t tau_threshold_bits(double tau, pc_dtype dt) {
+  if (dt == PC_F64) {
+    uint64_t b;
+    std::memcpy(&b, &tau, 8);
+    return b;
+  }
+  float f = (float)tau;
+  if ((double)f > tau) f = std::nextafterf(f, 0.0f);
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  return b;
+}
+
+bool tau_valid(const double* tau, int n) {
+  for (int i = 0; i < n; ++i) {
+    if (!std::isfinite(tau[i]) || !(tau[i] > 0)) return false;
+    if (i && !(tau[i] < tau[i - 1])) return false;
+  }
+  return true;
+}
+
+void make_geometry(int ndims, const int64_t* dims, int64_t d3[3], int64_t nb[3], int64_t* nbricks, int64_t* nchunks) {
+  for (int a = 0; a < 3; ++a) {
+    d3[a] = a < ndims ? dims[a] : 1;
+    nb[a] = a < ndims ? (d3[a] + 3) / 4 : 1;
+  }
+  *nbricks = nb[0] * nb[1] * nb[2];
+  *nchunks = (*nbricks + kChunk - 1) / kChunk;
+}
+
+}  // namespace
+
+struct pc_streams {
+  int device = 0;
+  int ndims = 0;
+  int64_t dims[3] = {1, 1, 1};
+  int64_t nb[3] = {1, 1, 1};
+  int64_t nbricks = 0, nchunks = 0;
+  pc_dtype dtype = PC_F32;
+  int n = 0;
+  double tau[kMaxComponents] = {};
+  int L[kMaxComponents] = {};
+  uint64_t words[kMaxComponents] = {};      // payload words per component
+  uint64_t word_base[kMaxComponents] = {};  // component's first word in d_payload
+  uint64_t counts[kMaxComponents][5] = {};
+  uint64_t* d_payload = nullptr;   // all components back to back
+  uint64_t* d_chunk_word = nullptr;  // [n][nchunks]
+  uint16_t* d_brick_len = nullptr;   // [n][nbricks]
+  CompDesc* d_desc = nullptr;        // [n]
+  unsigned int* d_err = nullptr;
+};
+
+namespace {
+
+void streams_release(pc_streams* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  cudaFree(s->d_payload);
+  cudaFree(s->d_chunk_word);
+  cudaFree(s->d_brick_len);
+  cudaFree(s->d_desc);
+  cudaFree(s->d_err);
+  delete s;
+}
+
+// Uploads the per-component descriptors the retrieval kernel reads.
+pc_status upload_desc(pc_streams* s, cudaStream_t st) {
+  std::vector<CompDesc> d(s->n);
+  for (int i = 0; i < s->n; ++i) {
+    d[i].payload = s->d_payload + s->word_base[i];
+    d[i].nwords = s->words[i];
+    d[i].chunk_word = s->d_chunk_word + (int64_t)i * s->nchunks;
+    d[i].brick_len = s->d_brick_len + (int64_t)i * s->nbricks;
+    d[i].L = s->L[i];
+    d[i].pad_ = 0;
+  }
+  CK(cudaMemcpyAsync(s->d_desc, d.data(), sizeof(CompDesc) * s->n, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+pc_status box_of(const pc_streams* s, const pc_box* box, int64_t lo[3], int64_t hi[3]) {
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = 0;
+    hi[a] = s->dims[a];
+    if (box && a < s->ndims) {
+      lo[a] = box->lo[a];
+      hi[a] = box->hi[a];
+      if (lo[a] < 0 || hi[a] > s->dims[a] || lo[a] >= hi[a]) return fail(PC_ERR_ARG, "box outside the field or empty");
+    }
+  }
+  return PC_OK;
+}
+
+// Runs Algorithm 2 on the box: components k0+1..k added into d_out (device).
+pc_status run_retrieve(const pc_streams* s, int k0, int k, const int64_t lo[3], const int64_t hi[3], void* d_out,
+                       int write, cudaStream_t st) {
+  RetrieveParams R;
+  std::memset(&R, 0, sizeof(R));
+  R.comp = s->d_desc;
+  for (int a = 0; a < 3; ++a) {
+    R.dims[a] = s->dims[a];
+    R.nb[a] = s->nb[a];
+    R.lo[a] = lo[a];
+    R.hi[a] = hi[a];
+    R.bl[a] = lo[a] / 4;
+    R.bn[a] = (hi[a] - 1) / 4 - R.bl[a] + 1;
+  }
+  R.nbricks = s->nbricks;
+  R.nchunks = s->nchunks;
+  R.k0 = k0;
+  R.k = k;
+  R.nbox = R.bn[0] * R.bn[1] * R.bn[2];
+  R.out = d_out;
+  R.write = write;
+  R.err = s->d_err;
+  if (k == k0 && write) {
+    if (k0 == 0) {
+      const size_t bytes = (size_t)((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])) * dsize(s->dtype);
+      CK(cudaMemsetAsync(d_out, 0, bytes, st));
+    }
+    return PC_OK;
+  }
+  CK(launch_retrieve(s->dtype, s->ndims, R, st));
+  return PC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pc_last_error(void) { return g_err.c_str(); }
+
+int pc_version(void) { return (int)kFormatVersion; }
+
+pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtype dtype, const double* tau, int n,
+                      void* cuda_stream, pc_streams** out) {
+  g_err.clear();
+  if (!out) return fail(PC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!field || !dims || !tau) return fail(PC_ERR_ARG, "NULL field, dims or tau");
+  if (ndims < 1 || ndims > 3) return fail(PC_ERR_ARG, "ndims must be 1, 2 or 3");
+  if (dtype != PC_F32 && dtype != PC_F64) return fail(PC_ERR_ARG, "dtype must be PC_F32 or PC_F64");
+  if (n < 1 || n > PC_MAX_COMPONENTS) return fail(PC_ERR_ARG, "n out of range");
+  for (int a = 0; a < ndims; ++a)
+    if (dims[a] < 1) return fail(PC_ERR_ARG, "extent < 1");
+  if (!tau_valid(tau, n)) return fail(PC_ERR_TAU_ORDER, "tolerances must be finite, positive, strictly decreasing");
+  if (ndims != 3) return fail(PC_ERR_ARG, "this build codes 3D fields only");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+
+  pc_streams* s = new pc_streams();
+  s->device = dev;
+  s->ndims = ndims;
+  s->dtype = dtype;
+  s->n = n;
+  make_geometry(ndims, dims, s->dims, s->nb, &s->nbricks, &s->nchunks);
+  const int64_t count = s->dims[0] * s->dims[1] * s->dims[2];
+  const int64_t nbr = s->nbricks, nch = s->nchunks;
+
+  CompressParams P;
+  std::memset(&P, 0, sizeof(P));
+  for (int a = 0; a < 3; ++a) {
+    P.dims[a] = s->dims[a];
+    P.nb[a] = s->nb[a];
+  }
+  P.nbricks = nbr;
+  P.nchunks = nch;
+  P.n = n;
+  for (int i = 0; i < n; ++i) {
+    s->tau[i] = tau[i];
+    s->L[i] = floor_log2_bits(tau[i]);
+    P.tau_bits[i] = tau_threshold_bits(tau[i], dtype);
+    P.L[i] = s->L[i];
+  }
+
+  pc_status rc = PC_OK;
+  {
+    Scratch scr(st);
+    cudaError_t e = cudaSuccess;
+#define SCR(ptr, bytes)                                             \
+  if (e == cudaSuccess) e = scr.get((void**)&(ptr), (size_t)(bytes));
+    const void* d_field = field;
+    void* staged = nullptr;
+    if (!is_device_ptr(field)) {  // host field: copy it in on the stream
+      SCR(staged, count * dsize(dtype));
+      if (e == cudaSuccess) e = cudaMemcpyAsync(staged, field, count * dsize(dtype), cudaMemcpyHostToDevice, st);
+      d_field = staged;
+    }
+    P.field = d_field;
+    uint32_t* chunk_nwords = nullptr;
+    uint64_t* chunk_pool = nullptr;
+    uint32_t* chunk_counts = nullptr;
+    uint64_t* totals = nullptr;
+    unsigned long long* counts = nullptr;
+    unsigned int* flags = nullptr;
+    unsigned long long* used = nullptr;
+    uint64_t* comp_base = nullptr;
+    SCR(chunk_nwords, 4 * n * nch);
+    SCR(chunk_pool, 8 * n * nch);
+    SCR(chunk_counts, 20 * n * nch);
+    SCR(totals, 8 * n);
+    SCR(counts, 8 * 5 * n);
+    SCR(flags, 16);
+    SCR(used, 16);
+    SCR(comp_base, 8 * n);
+#undef SCR
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_desc, sizeof(CompDesc) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 16);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
+    if (e != cudaSuccess) {
+      streams_release(s);
+      return cuda_fail(e, "allocation");
+    }
+    P.chunk_nwords = chunk_nwords;
+    P.chunk_pool = chunk_pool;
+    P.brick_len = s->d_brick_len;
+    P.chunk_counts = chunk_counts;
+    P.flags = flags;
+    P.pool_used = used;
+
+    std::vector<uint64_t> h_tot(n);
+    std::vector<unsigned long long> h_cnt(5 * n);
+    unsigned int h_flags = 0;
+    unsigned long long h_used = 0;
+    // the pool is shared by every call on this device: hold it until the
+    // packing kernel that reads it has finished (upload_desc synchronises)
+    std::unique_lock<std::mutex> pool_lock(g_mu);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      {
+        DevCtx& cx = g_ctx[dev & 127];
+        // first guess: two bytes of stream per input byte, plus chunk padding
+        const uint64_t want = attempt == 0 ? (uint64_t)(count * dsize(dtype) * 2 / 8 + 2 * n * nch + 1024)
+                                           : (uint64_t)(h_used + h_used / 8 + 1024);
+        if (cx.pool_words < want) {
+          if (cx.pool) cudaFree(cx.pool);
+          cx.pool = nullptr;
+          cx.pool_words = 0;
+          e = cudaMalloc((void**)&cx.pool, want * 8);
+          if (e != cudaSuccess) break;
+          cx.pool_words = want;
+        }
+        P.pool = cx.pool;
+        P.pool_words = cx.pool_words;
+      }
+      if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 16, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, 16, st);
+      if (e == cudaSuccess) e = launch_compress(dtype, ndims, P, st);
+      if (e == cudaSuccess)
+        e = launch_scan_chunks(chunk_nwords, s->d_chunk_word, totals, chunk_counts, counts, n, nch, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h_tot.data(), totals, 8 * n, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt.data(), counts, 8 * 5 * n, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, flags, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h_used, used, 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) break;
+      if (!(h_flags & kFlagPoolOverflow)) break;
+    }
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "compress");
+    } else if (h_flags & kFlagNonFinite) {
+      rc = fail(PC_ERR_NONFINITE, "the field holds a NaN or an infinity");
+    } else if (h_flags & kFlagPoolOverflow) {
+      rc = fail(PC_ERR_OOM, "scratch pool could not be sized");
+    } else {
+      uint64_t total = 0;
+      std::vector<uint64_t> base(n);
+      for (int i = 0; i < n; ++i) {
+        base[i] = total;
+        s->word_base[i] = total;
+        s->words[i] = h_tot[i];
+        total += h_tot[i];
+        for (int k = 0; k < 5; ++k) s->counts[i][k] = h_cnt[5 * i + k];
+      }
+      e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(comp_base, base.data(), 8 * n, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = launch_pack(P.pool, chunk_nwords, chunk_pool, s->d_chunk_word, comp_base, s->d_payload, n, nch, st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "pack");
+    }
+    if (rc == PC_OK) rc = upload_desc(s, st);  // synchronises: scratch is idle when freed
+  }
+  if (rc != PC_OK) {
+    streams_release(s);
+    return rc;
+  }
+  *out = s;
+  return PC_OK;
+}
+
+pc_status pc_query_k(const pc_streams* s, double tau, int* k_out) {
+  g_err.clear();
+  if (!s || !k_out) return fail(PC_ERR_ARG, "NULL argument");
+  if (!(tau >= 0) || std::isnan(tau)) return fail(PC_ERR_ARG, "tau must be a number >= 0");
+  for (int i = 0; i < s->n; ++i)
+    if (s->tau[i] <= tau) {
+      *k_out = i + 1;
+      return PC_OK;
+    }
+  return fail(PC_ERR_TOL_UNREACHABLE, "tolerance finer than the last component's");
+}
+
+static pc_status retrieve_common(const pc_streams* s, int k0, int k, const pc_box* box, void* buf, int read_in,
+                                 void* cuda_stream) {
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int64_t lo[3], hi[3];
+  pc_status r = box_of(s, box, lo, hi);
+  if (r != PC_OK) return r;
+  const size_t bytes = (size_t)((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])) * dsize(s->dtype);
+  if (is_device_ptr(buf)) return run_retrieve(s, k0, k, lo, hi, buf, 1, st);
+  Scratch scr(st);
+  void* d = nullptr;
+  CK(scr.get(&d, bytes));
+  if (read_in) CK(cudaMemcpyAsync(d, buf, bytes, cudaMemcpyHostToDevice, st));
+  r = run_retrieve(s, k0, k, lo, hi, d, 1, st);
+  if (r != PC_OK) return r;
+  CK(cudaMemcpyAsync(buf, d, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+pc_status pc_retrieve(const pc_streams* s, double tau, int k, const pc_box* box, void* out, void* cuda_stream) {
+  g_err.clear();
+  if (!s || !out) return fail(PC_ERR_ARG, "NULL argument");
+  if (tau >= 0) {
+    pc_status r = pc_query_k(s, tau, &k);
+    if (r != PC_OK) return r;
+  } else if (k < 0 || k > s->n) {
+    return fail(PC_ERR_ARG, "k out of range");
+  }
+  return retrieve_common(s, 0, k, box, out, 0, cuda_stream);
+}
+
+pc_status pc_refine(const pc_streams* s, int k0, int k, const pc_box* box, void* inout, void* cuda_stream) {
+  g_err.clear();
+  if (!s || !inout) return fail(PC_ERR_ARG, "NULL argument");
+  if (k0 < 0 || k < k0 || k > s->n) return fail(PC_ERR_ARG, "need 0 <= k0 <= k <= n");
+  return retrieve_common(s, k0, k, box, inout, 1, cuda_stream);
+}
+
+pc_status pc_stream_info(const pc_streams* s, int i, double* tau_i, uint64_t* bits, uint64_t* index_bytes) {
+  g_err.clear();
+  if (!s || i < 0 || i >= s->n) return fail(PC_ERR_ARG, "bad streams or component index");
+  if (tau_i) *tau_i = s->tau[i];
+  if (bits) *bits = s->words[i] * 64;
+  if (index_bytes) *index_bytes = (uint64_t)s->nchunks * 8 + (uint64_t)s->nbricks * 2;
+  return PC_OK;
+}
+
+pc_status pc_streams_shape(const pc_streams* s, int* ndims, int64_t* dims, pc_dtype* dtype, int* n) {
+  g_err.clear();
+  if (!s) return fail(PC_ERR_ARG, "NULL streams");
+  if (ndims) *ndims = s->ndims;
+  if (dims)
+    for (int a = 0; a < 3; ++a) dims[a] = s->dims[a];
+  if (dtype) *dtype = s->dtype;
+  if (n) *n = s->n;
+  return PC_OK;
+}
+
+pc_status pc_stream_counts(const pc_streams* s, int i, uint64_t counts[5]) {
+  g_err.clear();
+  if (!s || !counts || i < 0 || i >= s->n) return fail(PC_ERR_ARG, "bad arguments");
+  for (int k = 0; k < 5; ++k) counts[k] = s->counts[i][k];
+  return PC_OK;
+}
+
+pc_status pc_stream_device_ptrs(const pc_streams* s, int i, const uint64_t** payload, const uint64_t** chunk_word,
+                                const uint16_t** brick_len, uint64_t* payload_words, uint64_t* nchunks,
+                                uint64_t* nbricks) {
+  g_err.clear();
+  if (!s || i < 0 || i >= s->n) return fail(PC_ERR_ARG, "bad streams or component index");
+  if (payload) *payload = s->d_payload + s->word_base[i];
+  if (chunk_word) *chunk_word = s->d_chunk_word + (int64_t)i * s->nchunks;
+  if (brick_len) *brick_len = s->d_brick_len + (int64_t)i * s->nbricks;
+  if (payload_words) *payload_words = s->words[i];
+  if (nchunks) *nchunks = (uint64_t)s->nchunks;
+  if (nbricks) *nbricks = (uint64_t)s->nbricks;
+  return PC_OK;
+}
+
+// Serialized layout (little endian): a 64-byte header {magic, version, dtype,
+// ndims, n, 0, dims[3], nbricks, nchunks}, then per component {tau, words,
+// counts[5]} (56 bytes), then per component chunk_word[nchunks] (u64),
+// brick_len[nbricks] (u16, padded to 8 bytes) and payload[words] (u64).
+static size_t serialized_size(const pc_streams* s) {
+  size_t sz = 64 + 56 * (size_t)s->n;
+  for (int i = 0; i < s->n; ++i)
+    sz += 8 * (size_t)s->nchunks + (((size_t)s->nbricks * 2 + 7) & ~(size_t)7) + 8 * s->words[i];
+  return sz;
+}
+
+pc_status pc_streams_serialize(const pc_streams* s, void* h_buf, size_t* len, void* cuda_stream) {
+  g_err.clear();
+  if (!s || !len) return fail(PC_ERR_ARG, "NULL argument");
+  const size_t need = serialized_size(s);
+  if (!h_buf) {
+    *len = need;
+    return PC_OK;
+  }
+  if (*len < need) return fail(PC_ERR_ARG, "buffer too small");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  unsigned char* p = (unsigned char*)h_buf;
+  std::memset(p, 0, 64);
+  uint32_t hd[6] = {kMagic, kFormatVersion, (uint32_t)s->dtype, (uint32_t)s->ndims, (uint32_t)s->n, 0};
+  std::memcpy(p, hd, 24);
+  std::memcpy(p + 24, s->dims, 24);
+  std::memcpy(p + 48, &s->nbricks, 8);
+  std::memcpy(p + 56, &s->nchunks, 8);
+  p += 64;
+  for (int i = 0; i < s->n; ++i) {
+    std::memcpy(p, &s->tau[i], 8);
+    std::memcpy(p + 8, &s->words[i], 8);
+    std::memcpy(p + 16, s->counts[i], 40);
+    p += 56;
+  }
+  for (int i = 0; i < s->n; ++i) {
+    CK(cudaMemcpyAsync(p, s->d_chunk_word + (int64_t)i * s->nchunks, 8 * s->nchunks, cudaMemcpyDeviceToHost, st));
+    p += 8 * s->nchunks;
+    const size_t bl = (size_t)s->nbricks * 2;
+    CK(cudaMemcpyAsync(p, s->d_brick_len + (int64_t)i * s->nbricks, bl, cudaMemcpyDeviceToHost, st));
+    std::memset(p + bl, 0, ((bl + 7) & ~(size_t)7) - bl);
+    p += (bl + 7) & ~(size_t)7;
+    CK(cudaMemcpyAsync(p, s->d_payload + s->word_base[i], 8 * s->words[i], cudaMemcpyDeviceToHost, st));
+    p += 8 * s->words[i];
+  }
+  CK(cudaStreamSynchronize(st));
+  *len = need;
+  return PC_OK;
+}
+
+pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_stream, pc_streams** out) {
+  g_err.clear();
+  if (!h_buf || !out) return fail(PC_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (len < 64) return fail(PC_ERR_VERSION, "too short for a header");
+  const unsigned char* p = (const unsigned char*)h_buf;
+  uint32_t hd[6];
+  std::memcpy(hd, p, 24);
+  if (hd[0] != kMagic || hd[1] != kFormatVersion) return fail(PC_ERR_VERSION, "not a PCZ stream of this version");
+  const pc_dtype dt = (pc_dtype)hd[2];
+  const int ndims = (int)hd[3], n = (int)hd[4];
+  if ((dt != PC_F32 && dt != PC_F64) || ndims < 1 || ndims > 3 || n < 1 || n > PC_MAX_COMPONENTS)
+    return fail(PC_ERR_CORRUPT_STREAM, "bad header fields");
+  int64_t dims[3], nbr, nch;
+  std::memcpy(dims, p + 24, 24);
+  std::memcpy(&nbr, p + 48, 8);
+  std::memcpy(&nch, p + 56, 8);
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 1 || dims[a] > ((int64_t)1 << 40)) return fail(PC_ERR_CORRUPT_STREAM, "bad extents");
+  pc_streams* s = new pc_streams();
+  s->ndims = ndims;
+  s->dtype = dt;
+  s->n = n;
+  make_geometry(ndims, dims, s->dims, s->nb, &s->nbricks, &s->nchunks);
+  if (s->nbricks != nbr || s->nchunks != nch || ndims != 3) {
+    delete s;
+    return fail(PC_ERR_CORRUPT_STREAM, "brick counts do not match the extents");
+  }
+  size_t off = 64;
+  if (len < off + 56 * (size_t)n) {
+    delete s;
+    return fail(PC_ERR_CORRUPT_STREAM, "truncated");
+  }
+  uint64_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    std::memcpy(&s->tau[i], p + off, 8);
+    std::memcpy(&s->words[i], p + off + 8, 8);
+    std::memcpy(s->counts[i], p + off + 16, 40);
+    off += 56;
+    s->word_base[i] = total;
+    total += s->words[i];
+  }
+  if (!tau_valid(s->tau, n)) {
+    delete s;
+    return fail(PC_ERR_CORRUPT_STREAM, "bad tolerances");
+  }
+  for (int i = 0; i < n; ++i) s->L[i] = floor_log2_bits(s->tau[i]);
+  if (len != serialized_size(s)) {
+    delete s;
+    return fail(PC_ERR_CORRUPT_STREAM, "length does not match the header");
+  }
+  // index consistency on the host: chunk word offsets follow from the brick lengths
+  {
+    size_t q = off;
+    for (int i = 0; i < n; ++i) {
+      const uint64_t* cw = (const uint64_t*)(p + q);
+      const uint16_t* bl = (const uint16_t*)(p + q + 8 * nch);
+      uint64_t w = 0;
+      for (int64_t c = 0; c < nch; ++c) {
+        uint64_t bits = 0;
+        for (int64_t b = c * kChunk; b < nbr && b < (c + 1) * kChunk; ++b) bits += bl[b];
+        if (cw[c] != w) {
+          delete s;
+          return fail(PC_ERR_CORRUPT_STREAM, "chunk offsets inconsistent with brick lengths");
+        }
+        w += (bits + 63) / 64;
+      }
+      if (w != s->words[i]) {
+        delete s;
+        return fail(PC_ERR_CORRUPT_STREAM, "payload size inconsistent with brick lengths");
+      }
+      q += 8 * nch + (((size_t)nbr * 2 + 7) & ~(size_t)7) + 8 * s->words[i];
+    }
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  s->device = dev;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_desc, sizeof(CompDesc) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(s->d_chunk_word + (int64_t)i * nch, p + off, 8 * nch, cudaMemcpyHostToDevice, st);
+    off += 8 * nch;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->d_brick_len + (int64_t)i * nbr, p + off, 2 * nbr, cudaMemcpyHostToDevice, st);
+    off += ((size_t)nbr * 2 + 7) & ~(size_t)7;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->d_payload + s->word_base[i], p + off, 8 * s->words[i], cudaMemcpyHostToDevice, st);
+    off += 8 * s->words[i];
+  }
+  if (e != cudaSuccess) {
+    streams_release(s);
+    return cuda_fail(e, "deserialize upload");
+  }
+  pc_status r = upload_desc(s, st);
+  // every block must parse: one pass of Algorithm 2 over all components, no output
+  int64_t lo[3] = {0, 0, 0}, hi[3] = {s->dims[0], s->dims[1], s->dims[2]};
+  if (r == PC_OK) r = run_retrieve(s, 0, n, lo, hi, nullptr, 0, st);
+  unsigned int h_err = 0;
+  if (r == PC_OK) {
+    e = cudaMemcpyAsync(&h_err, s->d_err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) r = cuda_fail(e, "validation");
+  }
+  if (r == PC_OK && h_err) r = fail(PC_ERR_CORRUPT_STREAM, "a block does not parse");
+  if (r != PC_OK) {
+    streams_release(s);
+    return r;
+  }
+  *out = s;
+  return PC_OK;
+}
+
+void pc_streams_free(pc_streams* s) { streams_release(s); }
+
+pc_status pc_field_range(const void* d_field, int64_t count, pc_dtype dtype, void* cuda_stream, double* vmin,
+                         double* vmax) {
+  g_err.clear();
+  if (!d_field || count < 1 || !vmin || !vmax) return fail(PC_ERR_ARG, "bad arguments");
+  if (dtype != PC_F32 && dtype != PC_F64) return fail(PC_ERR_ARG, "bad dtype");
+  if (!is_device_ptr(d_field)) return fail(PC_ERR_ARG, "field must be device memory");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Scratch scr(st);
+  unsigned long long* enc = nullptr;
+  CK(scr.get((void**)&enc, 32));
+  unsigned int* flags = (unsigned int*)(enc + 2);
+  unsigned long long init[4] = {~0ull, 0ull, 0ull, 0ull};
+  CK(cudaMemcpyAsync(enc, init, 32, cudaMemcpyHostToDevice, st));
+  CK(launch_range(dtype, d_field, count, enc, flags, st));
+  unsigned long long h[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(h, enc, 24, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if ((unsigned int)h[2] & kFlagNonFinite) return fail(PC_ERR_NONFINITE, "the field holds a NaN or an infinity");
+  for (int w = 0; w < 2; ++w) {  // undo the order-preserving key
+    double v;
+    if (dtype == PC_F32) {
+      uint32_t k = (uint32_t)h[w];
+      uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+      float f;
+      std::memcpy(&f, &b, 4);
+      v = f;
+    } else {
+      uint64_t k = h[w];
+      uint64_t b = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+      std::memcpy(&v, &b, 8);
+    }
+    (w ? *vmax : *vmin) = v;
+  }
+  return PC_OK;
+}
+
+}  // extern "C"

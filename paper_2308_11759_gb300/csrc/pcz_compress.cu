@@ -1,0 +1,482 @@
+// pcz_compress.cu -- fused construction kernel: Algorithm 1 (Magri & Lindstrom,
+// Sec. 4.1) for every 4x4x4 brick of a 3D field, all n components in one pass.
+//
+// Per brick and component i the kernel computes the residual e = x - x~_{i-1}
+// (line 3), codes it with the PCZ coder at tau_i (line 4: y_i = C(e, tau_i)),
+// reconstructs x_i = D(y_i) from the coded planes (line 5) and adds it into
+// x~ (line 6).  x and x~ never leave registers, so the field is read once.
+//
+// Layout: one CTA per index chunk of 32 bricks (R15), 16 warps; a warp codes
+// two bricks, 16 lanes each; lane t of a brick holds the x-line y = t & 3,
+// z = t >> 2.  The y and z lifting passes and the coefficient reorder go
+// through a per-brick shared buffer.  Bit planes are formed with warp ballots
+// and each lane emits one plane (R11); the planes' significance counts and
+// bit offsets come from warp prefix scans.  The chunk's bits are assembled in
+// shared memory and appended to a scratch pool with one atomic per chunk;
+// pcz_misc.cu then scans the chunk sizes and packs the final streams.
+#include <climits>
+#include <type_traits>
+
+#include "pcz_device.cuh"
+#include "pcz_kernels.h"
+
+namespace pcz {
+
+__constant__ PermTable kPerm3 = make_perm(64);
+
+// Largest bit string of one brick and component: CODED with every plane
+// non-empty (each plane at most 2N + 1 bits) plus the header.
+template <typename T>
+__host__ __device__ constexpr int max_brick_bits3() {
+  return 2 + 3 + Fmt<T>::EBITS + Fmt<T>::P * (2 * 64 + 1);
+}
+
+template <typename T>
+__host__ __device__ constexpr int chunk_buf_words3() {  // u32 words, rounded to whole u64 words
+  return ((kChunk * max_brick_bits3<T>() + 63) / 64) * 2;
+}
+
+constexpr int kCompressThreads3 = 512;
+
+template <typename T>
+constexpr size_t compress_smem3() {
+  using S = typename Fmt<T>::S;
+  return (size_t)chunk_buf_words3<T>() * 4      // chunk bit buffer
+         + (size_t)kChunk * 64 * sizeof(S)     // one brick buffer per brick
+         + 32 * 4 * 5                          // lengths, offsets, modes, escalations, violations
+         + 16;                                 // pool base
+}
+
+// Writes one plane's code (R11) at bit offset o of buf: n verbatim bits of W,
+// then a test bit 1 and the run up to each newly significant coefficient, and
+// a closing test 0 (a zero bit, already clear) while n < N.
+template <int N>
+__device__ __forceinline__ void write_plane(uint32_t* buf, uint32_t o, uint64_t W, int n) {
+  if (n > 0) or_bits(buf, o, W & low_mask64(n));
+  if (n >= N) return;
+  o += n;
+  uint64_t w = n >= 64 ? 0ull : (W >> n);
+  uint64_t a0 = 0, a1 = 0, a2 = 0;
+  int rel = 0;
+  for (int it = 0; it < 64 && w; ++it) {  // one pass per set bit
+    int tz = __ffsll((long long)w) - 1;
+    int r1 = rel, r2 = rel + 1 + tz;  // the test bit and the coefficient's 1
+    if (r1 < 64) a0 |= 1ull << r1; else if (r1 < 128) a1 |= 1ull << (r1 - 64); else a2 |= 1ull << (r1 - 128);
+    if (r2 < 64) a0 |= 1ull << r2; else if (r2 < 128) a1 |= 1ull << (r2 - 64); else a2 |= 1ull << (r2 - 128);
+    rel = r2 + 1;
+    w = tz >= 63 ? 0ull : (w >> (tz + 1));
+  }
+  or_bits(buf, o, a0);
+  or_bits(buf, o + 64, a1);
+  or_bits(buf, o + 128, a2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const CompressParams P) {
+  using F = Fmt<T>;
+  using U = typename F::U;
+  using S = typename F::S;
+  constexpr int N = 64;
+  constexpr int Q = F::P - 2 - Geo<3>::G;  // quantisation bits (R6)
+  constexpr int C = Geo<3>::C;             // guard planes (R10)
+  constexpr int HDR = 2 + 3 + F::EBITS;    // mode, escalation, block exponent
+  constexpr int LEN_RAW = 2 + N * F::P;
+  constexpr int BUFW = chunk_buf_words3<T>();
+  constexpr unsigned FULL = 0xffffffffu;
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* cbuf = reinterpret_cast<uint32_t*>(smem);
+  S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4);
+  int* s_len = reinterpret_cast<int*>(bbuf + kChunk * 64);
+  int* s_off = s_len + 32;
+  int* s_mode = s_off + 32;
+  int* s_esc = s_mode + 32;
+  int* s_viol = s_esc + 32;
+  unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_viol + 32);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int h = lane >> 4, t = lane & 15;
+  const unsigned HALF = h ? 0xffff0000u : 0x0000ffffu;
+  const int64_t chunk = blockIdx.x;
+  const int slot = warp * 2 + h;
+  const int64_t b = chunk * kChunk + slot;
+  const bool have = b < P.nbricks;
+
+  for (int w = tid; w < BUFW; w += kCompressThreads3) cbuf[w] = 0u;
+
+  int64_t bx = 0, by = 0, bz = 0;
+  if (have) {
+    bx = b % P.nb[0];
+    int64_t r = b / P.nb[0];
+    by = r % P.nb[1];
+    bz = r / P.nb[1];
+  }
+  const int ly = t & 3, lz = t >> 2;
+  int nvx = 4, nvy = 4, nvz = 4;  // in-field extent of the brick per axis
+  if (have) {
+    nvx = (int)(P.dims[0] - 4 * bx < 4 ? P.dims[0] - 4 * bx : 4);
+    nvy = (int)(P.dims[1] - 4 * by < 4 ? P.dims[1] - 4 * by : 4);
+    nvz = (int)(P.dims[2] - 4 * bz < 4 ? P.dims[2] - 4 * bz : 4);
+  }
+  const bool line_in = have && ly < nvy && lz < nvz;
+  // R4: a lane outside the field takes the nearest in-field line's values
+  const int srcl = 16 * h + min(ly, nvy - 1) + 4 * min(lz, nvz - 1);
+  const bool partial = have && (nvx < 4 || nvy < 4 || nvz < 4);
+  const bool any_partial = __any_sync(FULL, partial);
+
+  T x[4], xt[4], e[4];
+  {
+    const T* field = reinterpret_cast<const T*>(P.field);
+    if (have) {
+      const int64_t gy = 4 * by + min(ly, nvy - 1), gz = 4 * bz + min(lz, nvz - 1);
+      const T* row = field + (gz * P.dims[1] + gy) * P.dims[0] + 4 * bx;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) x[m] = row[min(m, nvx - 1)];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) x[m] = T(0);
+    }
+  }
+  {
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (line_in && m < nvx && not_finite<T>(x[m])) bad = true;
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(P.flags, kFlagNonFinite);
+  }
+  // Algorithm 1, line 1: x~ = 0; the first residual is x - 0
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    xt[m] = T(0);
+    e[m] = F::sub(x[m], T(0));
+  }
+  S* mybuf = bbuf + slot * 64;
+  int pos_r[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) pos_r[j] = kPerm3.pos[t + 16 * j];
+  const int xx = t & 3, yq = t >> 2;  // lane roles in the y and z passes
+
+  for (int i = 0; i < P.n; ++i) {  // line 2
+    const U tb = (U)P.tau_bits[i];
+    if (any_partial) {  // R4 padding of the residual
+      const T last = nvx == 1 ? e[0] : nvx == 2 ? e[1] : nvx == 3 ? e[2] : e[3];
+#pragma unroll
+      for (int m = 1; m < 4; ++m)
+        if (m >= nvx) e[m] = last;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) e[m] = __shfl_sync(FULL, e[m], srcl);
+    }
+    // R5: a brick whose residual meets tau_i on every in-field value is ZERO
+    bool small = true;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (line_in && m < nvx && !within<T>(e[m], tb)) small = false;
+    // (every lane takes part in each vote: a vote behind && or || would be
+    // skipped by one half of the warp and leave the other half waiting)
+    const unsigned big_votes = __ballot_sync(FULL, !small);
+    const bool zero_blk = !have || ((big_votes & HALF) == 0u);
+    bool nf = false;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) nf |= not_finite<T>(e[m]);
+    const unsigned nf_votes = __ballot_sync(FULL, nf);
+    const bool raw_forced = !zero_blk && ((nf_votes & HALF) != 0u);
+
+    // R6: block exponent and exact quantisation
+    int be = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) be = max(be, biased_exp<T>(F::bits(e[m])));
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) be = max(be, __shfl_xor_sync(FULL, be, o));
+    const int emax = block_emax_from_be<T>(be);
+    const int s = Q - emax;
+    S q[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) q[m] = quantize<T>(F::bits(e[m]), s);
+
+    // R7: lifting along x (in the lane), y and z (shared buffer)
+    lift_fwd(q[0], q[1], q[2], q[3]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) mybuf[4 * t + m] = q[m];
+    __syncwarp();
+    {
+      S a = mybuf[xx + 16 * yq], bq = mybuf[xx + 4 + 16 * yq], c = mybuf[xx + 8 + 16 * yq], d = mybuf[xx + 12 + 16 * yq];
+      lift_fwd(a, bq, c, d);
+      mybuf[xx + 16 * yq] = a; mybuf[xx + 4 + 16 * yq] = bq; mybuf[xx + 8 + 16 * yq] = c; mybuf[xx + 12 + 16 * yq] = d;
+    }
+    __syncwarp();
+    {
+      S a = mybuf[xx + 4 * yq], bq = mybuf[xx + 4 * yq + 16], c = mybuf[xx + 4 * yq + 32], d = mybuf[xx + 4 * yq + 48];
+      lift_fwd(a, bq, c, d);
+      mybuf[xx + 4 * yq] = a; mybuf[xx + 4 * yq + 16] = bq; mybuf[xx + 4 * yq + 32] = c; mybuf[xx + 4 * yq + 48] = d;
+    }
+    __syncwarp();
+    // R8, R9: coded order, negabinary.  Lane t holds coefficients t + 16j.
+    U u[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = nb_fwd<T>(mybuf[pos_r[j]]);
+    __syncwarp();
+
+    // R10, R13: lowest coded plane; lowered until Eq. 1 holds in T
+    const int L = P.L[i];
+    int esc = 0, p = 0;
+    bool done = zero_blk || raw_forced, pass = false;
+    T xtc[4], ec[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) { xtc[m] = xt[m]; ec[m] = e[m]; }
+    for (int round = 0; round < 8; ++round) {  // esc runs 0..7: at most 8 rounds
+      const bool active = !done;
+      const int pp = min(max(L + s - C - esc, 0), F::P);
+      const U keep = pp >= F::P ? U(0) : (U)~((U(1) << pp) - 1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) mybuf[pos_r[j]] = nb_inv<T>((U)(u[j] & keep));
+      __syncwarp();
+      {
+        S a = mybuf[xx + 4 * yq], bq = mybuf[xx + 4 * yq + 16], c = mybuf[xx + 4 * yq + 32], d = mybuf[xx + 4 * yq + 48];
+        lift_inv(a, bq, c, d);
+        mybuf[xx + 4 * yq] = a; mybuf[xx + 4 * yq + 16] = bq; mybuf[xx + 4 * yq + 32] = c; mybuf[xx + 4 * yq + 48] = d;
+      }
+      __syncwarp();
+      {
+        S a = mybuf[xx + 16 * yq], bq = mybuf[xx + 4 + 16 * yq], c = mybuf[xx + 8 + 16 * yq], d = mybuf[xx + 12 + 16 * yq];
+        lift_inv(a, bq, c, d);
+        mybuf[xx + 16 * yq] = a; mybuf[xx + 4 + 16 * yq] = bq; mybuf[xx + 8 + 16 * yq] = c; mybuf[xx + 12 + 16 * yq] = d;
+      }
+      __syncwarp();
+      S r[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) r[m] = mybuf[4 * t + m];
+      __syncwarp();
+      lift_inv(r[0], r[1], r[2], r[3]);
+      bool ok = true;
+      T xtn[4], en[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const T xi = F::val(dequantize_bits<T>(r[m], s));  // line 5: x_i = D(y_i)
+        xtn[m] = F::add(xt[m], xi);                        // line 6 (candidate)
+        en[m] = F::sub(x[m], xtn[m]);                      // the next residual
+        if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
+      }
+      const bool pass_h = (__ballot_sync(FULL, !ok) & HALF) == 0u;
+      if (active) {
+        if (pass_h) {
+          pass = true;
+          done = true;
+          p = pp;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) { xtc[m] = xtn[m]; ec[m] = en[m]; }
+        } else if (esc == 7 || pp == 0) {
+          done = true;
+        } else {
+          ++esc;
+        }
+      }
+      if (__all_sync(FULL, done)) break;
+    }
+
+    // R11: plane words of the coded coefficients and the CODED length
+    U orr = u[0] | u[1] | u[2] | u[3];
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) orr |= (U)__shfl_xor_sync(FULL, orr, o);
+    const int top = orr ? (F::P - 1 - F::clz(orr)) : -1;
+    const int K = (pass && top >= p) ? top - p + 1 : 0;          // planes from top down to p
+    const int Z = pass ? (F::P - 1 - max(top, p - 1)) : 0;       // empty planes above: one bit each
+    const int KA = __shfl_sync(FULL, K, 0), KB = __shfl_sync(FULL, K, 16);
+    const int topA = __shfl_sync(FULL, top, 0), topB = __shfl_sync(FULL, top, 16);
+    uint64_t WA0 = 0, WA1 = 0, WB0 = 0, WB1 = 0;
+    if (KA > 0 || KB > 0) {
+      const int phi = max(KA ? topA : -1, KB ? topB : -1);
+      const int plo = min(KA ? topA - KA + 1 : INT_MAX, KB ? topB - KB + 1 : INT_MAX);
+      for (int pl = phi; pl >= plo; --pl) {
+        const unsigned b0 = __ballot_sync(FULL, (unsigned)(u[0] >> pl) & 1u);
+        const unsigned b1 = __ballot_sync(FULL, (unsigned)(u[1] >> pl) & 1u);
+        const unsigned b2 = __ballot_sync(FULL, (unsigned)(u[2] >> pl) & 1u);
+        const unsigned b3 = __ballot_sync(FULL, (unsigned)(u[3] >> pl) & 1u);
+        const uint64_t wa = (uint64_t)__byte_perm(b0, b1, 0x5410) | ((uint64_t)__byte_perm(b2, b3, 0x5410) << 32);
+        const uint64_t wb = (uint64_t)__byte_perm(b0, b1, 0x7632) | ((uint64_t)__byte_perm(b2, b3, 0x7632) << 32);
+        const int ka = topA - pl, kb = topB - pl;
+        if (ka >= 0 && ka < KA && (ka & 31) == lane) { if (ka >> 5) WA1 = wa; else WA0 = wa; }
+        if (kb >= 0 && kb < KB && (kb & 31) == lane) { if (kb >> 5) WB1 = wb; else WB0 = wb; }
+      }
+    }
+    // per brick: n before each plane (prefix max) and its bit offset (prefix sum)
+    int nA0 = 0, nA1 = 0, nB0 = 0, nB1 = 0, oA0 = 0, oA1 = 0, oB0 = 0, oB1 = 0, totA = 0, totB = 0;
+#pragma unroll
+    for (int hb = 0; hb < 2; ++hb) {
+      const int KX = hb ? KB : KA;
+      int cmax = 0, csum = 0;
+#pragma unroll
+      for (int rd = 0; rd < 2; ++rd) {
+        if (rd == 1 && KX <= 32) break;
+        const int k = lane + 32 * rd;
+        const uint64_t W = hb ? (rd ? WB1 : WB0) : (rd ? WA1 : WA0);
+        const bool act = k < KX;
+        const int hi = (act && W) ? 64 - __clzll((long long)W) : 0;
+        int v = hi;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(FULL, v, o);
+          if (lane >= o) v = max(v, y);
+        }
+        int ex = __shfl_up_sync(FULL, v, 1);
+        if (lane == 0) ex = 0;
+        const int nn = max(ex, cmax);
+        const int len = act ? plane_len<N>(W, nn) : 0;
+        int sum = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(FULL, sum, o);
+          if (lane >= o) sum += y;
+        }
+        const int off = sum - len + csum;
+        if (hb) { if (rd) { nB1 = nn; oB1 = off; } else { nB0 = nn; oB0 = off; } }
+        else { if (rd) { nA1 = nn; oA1 = off; } else { nA0 = nn; oA0 = off; } }
+        cmax = max(cmax, __shfl_sync(FULL, v, 31));
+        csum += __shfl_sync(FULL, sum, 31);
+      }
+      if (hb) totB = csum; else totA = csum;
+    }
+    const int lenC = HDR + Z + (h ? totB : totA);
+
+    // R14: RAW replaces a longer CODED brick only if it also meets tau_i
+    bool raw_ok = false;
+    if (__any_sync(FULL, pass && lenC > LEN_RAW)) {
+      bool ok = true;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const T a = F::add(xt[m], e[m]);
+        if (line_in && m < nvx && !within<T>(F::sub(x[m], a), tb)) ok = false;
+      }
+      raw_ok = (__ballot_sync(FULL, !ok) & HALF) == 0u;
+    }
+    const int mode = zero_blk ? kModeZero : (pass && !(lenC > LEN_RAW && raw_ok)) ? kModeCoded : kModeRaw;
+    const int blen = !have ? 0 : mode == kModeZero ? 2 : mode == kModeRaw ? LEN_RAW : lenC;
+
+    // line 6: commit x~_i and the next residual; keep e_i for a RAW brick
+    T e_raw[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      e_raw[m] = e[m];
+      if (mode == kModeCoded) {
+        xt[m] = xtc[m];
+        e[m] = ec[m];
+      } else if (mode == kModeRaw) {
+        xt[m] = F::add(xt[m], e_raw[m]);
+        e[m] = F::sub(x[m], xt[m]);
+      }
+    }
+    int viol = 0;  // Eq. 1 failures left (only a RAW brick can have them)
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (line_in && m < nvx && !within<T>(e[m], tb)) ++viol;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) viol += __shfl_xor_sync(FULL, viol, o);
+
+    if (t == 0) {
+      s_len[slot] = blen;
+      s_mode[slot] = have ? mode : -1;
+      s_esc[slot] = (have && mode == kModeCoded) ? esc : 0;
+      s_viol[slot] = have ? viol : 0;
+    }
+    __syncthreads();
+    if (warp == 0) {  // chunk layout: brick offsets, pool space, index entries
+      const int l0 = s_len[lane];
+      int incl = l0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      s_off[lane] = incl - l0;
+      const int total = __shfl_sync(FULL, incl, 31);
+      const unsigned nw = (unsigned)((total + 63) >> 6);
+      const int md = s_mode[lane];
+      const unsigned cz = __popc(__ballot_sync(FULL, md == kModeZero));
+      const unsigned cc = __popc(__ballot_sync(FULL, md == kModeCoded));
+      const unsigned cr = __popc(__ballot_sync(FULL, md == kModeRaw));
+      int se = s_esc[lane], sv = s_viol[lane];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        se += __shfl_xor_sync(FULL, se, o);
+        sv += __shfl_xor_sync(FULL, sv, o);
+      }
+      if (lane == 0) {
+        unsigned long long base = nw ? atomicAdd(P.pool_used, (unsigned long long)nw) : 0ull;
+        if (base + nw > P.pool_words) {
+          atomicOr(P.flags, kFlagPoolOverflow);
+          base = ~0ull;
+        }
+        *s_base = base;
+        const int64_t ci = (int64_t)i * P.nchunks + chunk;
+        P.chunk_nwords[ci] = nw;
+        P.chunk_pool[ci] = base;
+        uint32_t* cnt = P.chunk_counts + ci * 5;
+        cnt[0] = cz;
+        cnt[1] = cc;
+        cnt[2] = cr;
+        cnt[3] = (uint32_t)se;
+        cnt[4] = (uint32_t)sv;
+      }
+      const int64_t bb = chunk * kChunk + lane;
+      if (bb < P.nbricks) P.brick_len[(int64_t)i * P.nbricks + bb] = (uint16_t)l0;
+    }
+    __syncthreads();
+
+    // write this component's bits of the two bricks into the chunk buffer
+    const uint32_t boff = (uint32_t)s_off[slot];
+    if (have && mode == kModeRaw) {
+      if (t == 0) or_bits(cbuf, boff, (uint64_t)kModeRaw);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) or_bits(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(e_raw[m]));
+    } else if (have && mode == kModeCoded && t == 0) {
+      or_bits(cbuf, boff, (uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5));
+    }
+    const int modeA = __shfl_sync(FULL, mode, 0), modeB = __shfl_sync(FULL, mode, 16);
+    const int ZA = __shfl_sync(FULL, Z, 0), ZB = __shfl_sync(FULL, Z, 16);
+    const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
+    if (haveA && modeA == kModeCoded) {
+      const uint32_t base = (uint32_t)s_off[warp * 2] + HDR + ZA;
+      if (lane < KA) write_plane<N>(cbuf, base + oA0, WA0, nA0);
+      if (lane + 32 < KA) write_plane<N>(cbuf, base + oA1, WA1, nA1);
+    }
+    if (haveB && modeB == kModeCoded) {
+      const uint32_t base = (uint32_t)s_off[warp * 2 + 1] + HDR + ZB;
+      if (lane < KB) write_plane<N>(cbuf, base + oB0, WB0, nB0);
+      if (lane + 32 < KB) write_plane<N>(cbuf, base + oB1, WB1, nB1);
+    }
+    __syncthreads();
+    {  // append the chunk to the pool and clear the buffer for the next component
+      const unsigned long long base = *s_base;
+      const int total = s_off[31] + s_len[31];
+      const int nw = (total + 63) >> 6;
+      uint64_t* b64 = reinterpret_cast<uint64_t*>(cbuf);
+      for (int w = tid; w < nw; w += kCompressThreads3) {
+        if (base != ~0ull) P.pool[base + w] = b64[w];
+        b64[w] = 0ull;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int compress_block_threads(int ndims) { return kCompressThreads3; }
+
+size_t compress_smem_bytes(int dtype, int ndims) {
+  return dtype == 1 ? compress_smem3<float>() : compress_smem3<double>();
+}
+
+template <typename T>
+static cudaError_t launch_compress_t(const CompressParams& p, cudaStream_t s) {
+  const size_t smem = compress_smem3<T>();
+  cudaError_t e = cudaFuncSetAttribute(k_compress3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (p.nchunks == 0) return cudaSuccess;
+  k_compress3<T><<<(unsigned)p.nchunks, kCompressThreads3, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaStream_t s) {
+  if (ndims != 3) return cudaErrorNotSupported;
+  return dtype == 1 ? launch_compress_t<float>(p, s) : launch_compress_t<double>(p, s);
+}
+
+}  // namespace pcz

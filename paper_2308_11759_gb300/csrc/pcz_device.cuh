@@ -1,0 +1,292 @@
+// pcz_device.cuh -- device-side building blocks of the PCZ block coder used as
+// the compressor C / decompressor D of the multi-component framework
+// (Algorithm 1 and 2 of Magri & Lindstrom, Sec. 4).  GPU path only.
+//
+// The coder is zfp-style (Sec. 4.4, Sec. 6.1): one exponent per 4^d brick and
+// component, an exactly invertible integer lifting transform, negabinary
+// coefficients and group-tested bit planes (Sec. 2).  The paper does not fix
+// the coder's internals; the project rules R4..R15 do, and each is restated
+// where it is implemented.  All floating-point work here is IEEE
+// round-to-nearest with no contraction: the only arithmetic on T values is
+// one add or one subtract (explicit _rn intrinsics); scaling and conversions
+// are done on the bit patterns with integer operations.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda_runtime.h>
+
+#include "pcz_kernels.h"
+
+namespace pcz {
+constexpr int kModeZero = 0, kModeCoded = 1, kModeRaw = 2;
+
+// ---------------------------------------------------------------------------
+// Field types.  P = integer width = bits of T.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Fmt;
+
+template <>
+struct Fmt<float> {
+  using U = uint32_t;
+  using S = int32_t;
+  static constexpr int P = 32;
+  static constexpr int MANT = 24;    // significand bits, hidden bit included
+  static constexpr int EMIN = -125;  // frexp exponent of the smallest normal
+  static constexpr int EBITS = 8;    // stored block exponent width
+  static constexpr int EBIAS = 126;  // stored = emax + EBIAS
+  static constexpr int BIAS = 127;   // IEEE exponent bias
+  static constexpr int EXPW = 8;     // IEEE exponent field width
+  static constexpr U SIGN = 0x80000000u, ABS = 0x7FFFFFFFu, INF = 0x7F800000u;
+  static constexpr U NBM = 0xAAAAAAAAu;
+  __device__ static U bits(float v) { return __float_as_uint(v); }
+  __device__ static float val(U b) { return __uint_as_float(b); }
+  __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+  __device__ static int clz(U a) { return __clz(a); }
+};
+
+template <>
+struct Fmt<double> {
+  using U = uint64_t;
+  using S = int64_t;
+  static constexpr int P = 64;
+  static constexpr int MANT = 53;
+  static constexpr int EMIN = -1021;
+  static constexpr int EBITS = 11;
+  static constexpr int EBIAS = 1022;
+  static constexpr int BIAS = 1023;
+  static constexpr int EXPW = 11;
+  static constexpr U SIGN = 0x8000000000000000ull, ABS = 0x7FFFFFFFFFFFFFFFull, INF = 0x7FF0000000000000ull;
+  static constexpr U NBM = 0xAAAAAAAAAAAAAAAAull;
+  __device__ static U bits(double v) { return (U)__double_as_longlong(v); }
+  __device__ static double val(U b) { return __longlong_as_double((long long)b); }
+  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+  __device__ static int clz(U a) { return __clzll((long long)a); }
+};
+
+// Brick geometry for dimensionality D: N = 4^D coefficients, G = 2D headroom
+// bits for the forward transform's growth (R6), C guard planes (R10): the
+// smallest c with 2^c above (2/3) * 2.75^D, the inverse transform's worst-case
+// error per unit of truncated coefficient.
+template <int D>
+struct Geo {
+  static constexpr int N = D == 1 ? 4 : D == 2 ? 16 : 64;
+  static constexpr int G = 2 * D;
+  static constexpr int C = D == 1 ? 1 : D == 2 ? 3 : 4;
+};
+
+// ---------------------------------------------------------------------------
+// Wrapping P-bit integer arithmetic (two's complement, modulo 2^P).
+// ---------------------------------------------------------------------------
+template <typename S>
+__device__ __forceinline__ S wadd(S a, S b) {
+  using U = typename std::make_unsigned<S>::type;
+  return (S)((U)a + (U)b);
+}
+template <typename S>
+__device__ __forceinline__ S wsub(S a, S b) {
+  using U = typename std::make_unsigned<S>::type;
+  return (S)((U)a - (U)b);
+}
+
+// R7: forward lifting of one 4-vector: integer Haar on the pairs, Haar on the
+// pair means, then the second difference and the fine slope minus half the
+// coarse slope.  a,b,c,d -> (mean, coarse slope, e1, e2).
+template <typename S>
+__device__ __forceinline__ void lift_fwd(S& a, S& b, S& c, S& d) {
+  S d1 = wsub(b, a);
+  S s1 = wadd(a, d1 >> 1);
+  S d2 = wsub(d, c);
+  S s2 = wadd(c, d2 >> 1);
+  S d0 = wsub(s2, s1);
+  S s0 = wadd(s1, d0 >> 1);
+  S e2 = wsub(d2, d1);
+  S e1 = wsub(d1, d0 >> 1);
+  a = s0;
+  b = d0;
+  c = e1;
+  d = e2;
+}
+
+// R7 inverse: the forward steps replayed backwards with opposite signs.
+template <typename S>
+__device__ __forceinline__ void lift_inv(S& a, S& b, S& c, S& d) {
+  S s0 = a, d0 = b, e1 = c, e2 = d;
+  S d1 = wadd(e1, d0 >> 1);
+  S d2 = wadd(e2, d1);
+  S s1 = wsub(s0, d0 >> 1);
+  S s2 = wadd(s1, d0);
+  a = wsub(s1, d1 >> 1);
+  b = wadd(a, d1);
+  c = wsub(s2, d2 >> 1);
+  d = wadd(c, d2);
+}
+
+// R9: negabinary map and its inverse, modulo 2^P.
+template <typename T>
+__device__ __forceinline__ typename Fmt<T>::U nb_fwd(typename Fmt<T>::S q) {
+  using F = Fmt<T>;
+  return (typename F::U)(((typename F::U)q + F::NBM) ^ F::NBM);
+}
+template <typename T>
+__device__ __forceinline__ typename Fmt<T>::S nb_inv(typename Fmt<T>::U u) {
+  using F = Fmt<T>;
+  return (typename F::S)((u ^ F::NBM) - F::NBM);
+}
+
+// IEEE biased exponent field of a bit pattern.
+template <typename T>
+__device__ __forceinline__ int biased_exp(typename Fmt<T>::U b) {
+  using F = Fmt<T>;
+  return (int)((b >> (F::MANT - 1)) & ((1u << F::EXPW) - 1));
+}
+
+// R6: block exponent from the largest biased exponent over the brick: emax is
+// the frexp exponent of the largest magnitude, floored at the smallest normal's
+// (subnormals and zeros carry biased exponent 0).
+template <typename T>
+__device__ __forceinline__ int block_emax_from_be(int be_max) {
+  using F = Fmt<T>;
+  return (be_max > 1 ? be_max : 1) - (F::BIAS - 1);
+}
+
+// R6: q = sign(e) * floor(|e| * 2^s), computed exactly on the bit pattern:
+// |e| = m * 2^ex with m the integer significand.
+template <typename T>
+__device__ __forceinline__ typename Fmt<T>::S quantize(typename Fmt<T>::U b, int s) {
+  using F = Fmt<T>;
+  using U = typename F::U;
+  using S = typename F::S;
+  int be = biased_exp<T>(b);
+  U m = b & ((U(1) << (F::MANT - 1)) - 1);
+  if (be) m |= U(1) << (F::MANT - 1);
+  int ex = (be ? be : 1) - F::BIAS - (F::MANT - 1);
+  int sh = ex + s;
+  U a;
+  if (sh >= 0)
+    a = sh >= F::P ? U(0) : (m << sh);
+  else
+    a = -sh >= F::P ? U(0) : (m >> (-sh));
+  S q = (S)a;
+  return (b & F::SIGN) ? (S)(0 - (U)q) : q;
+}
+
+// R13: the T value nearest to q * 2^-s (ties to even, one rounding, IEEE signed
+// zero, +-inf beyond the largest finite value), as a bit pattern.
+template <typename T>
+__device__ __forceinline__ typename Fmt<T>::U dequantize_bits(typename Fmt<T>::S q, int s) {
+  using F = Fmt<T>;
+  using U = typename F::U;
+  if (q == 0) return U(0);
+  U a = q < 0 ? (U)(U(0) - (U)q) : (U)q;
+  int nb = F::P - F::clz(a);            // bit length of |q|
+  int E = nb - s;                       // frexp exponent of the exact value
+  int qe = (E > F::EMIN ? E : F::EMIN) - F::MANT;  // exponent of the last place
+  int sh = qe + s;                      // low bits of |q| below that place
+  U r;
+  if (sh <= 0) {
+    r = a << (-sh);
+  } else if (sh > F::P) {
+    r = 0;
+  } else if (sh == F::P) {
+    r = a > (U(1) << (F::P - 1)) ? U(1) : U(0);
+  } else {
+    r = a >> sh;
+    U rem = a & ((U(1) << sh) - 1);
+    U half = U(1) << (sh - 1);
+    if (rem > half || (rem == half && (r & 1))) r += 1;
+  }
+  int ef = qe - (F::EMIN - F::MANT);    // biased exponent - 1 for a normal result
+  U out;
+  if (ef >= (1 << F::EXPW) - 2) {
+    out = F::INF;
+  } else {
+    out = ((U)ef << (F::MANT - 1)) + r;  // a carry out of r bumps the exponent
+    if (out > F::INF) out = F::INF;
+  }
+  return q < 0 ? (out | F::SIGN) : out;
+}
+
+// |e| <= tau on bit patterns: tb is the pattern of the largest T value not
+// above tau, so the comparison is exact; NaN and +-inf fail it.
+template <typename T>
+__device__ __forceinline__ bool within(T e, typename Fmt<T>::U tb) {
+  using F = Fmt<T>;
+  return (F::bits(e) & F::ABS) <= tb;
+}
+
+template <typename T>
+__device__ __forceinline__ bool not_finite(T v) {
+  using F = Fmt<T>;
+  return (F::bits(v) & F::INF) == F::INF;
+}
+
+// ---------------------------------------------------------------------------
+// R8: sequency order of the 4^3 coefficients, ties by brick position.
+// kPerm3.pos[r] = brick position of the r-th coded coefficient.  Built at
+// compile time by ranking every position.
+// ---------------------------------------------------------------------------
+struct PermTable {
+  int8_t pos[64];
+};
+
+__host__ __device__ constexpr int seq_key(int p) { return (p & 3) + ((p >> 2) & 3) + (p >> 4); }
+
+__host__ __device__ constexpr PermTable make_perm(int n) {
+  PermTable t{};
+  for (int p = 0; p < n; ++p) {
+    int rank = 0;
+    for (int q = 0; q < n; ++q)
+      if (seq_key(q) < seq_key(p) || (seq_key(q) == seq_key(p) && q < p)) ++rank;
+    t.pos[rank] = (int8_t)p;
+  }
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Bit writes into a shared-memory bit buffer (bit b = bit b%32 of word b/32):
+// OR v into bits [off, off + 64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void or_bits(uint32_t* buf, uint32_t off, uint64_t v) {
+  if (!v) return;
+  uint32_t w = off >> 5, sh = off & 31;
+  uint64_t lo = v << sh;
+  uint32_t hi = sh ? (uint32_t)(v >> (64 - sh)) : 0u;
+  if ((uint32_t)lo) atomicOr(buf + w, (uint32_t)lo);
+  if ((uint32_t)(lo >> 32)) atomicOr(buf + w + 1, (uint32_t)(lo >> 32));
+  if (hi) atomicOr(buf + w + 2, hi);
+}
+
+// 64 bits of a word stream starting at bit pos (bit b = bit b%64 of word
+// b/64); words at or beyond nwords read as zero.
+__device__ __forceinline__ uint64_t peek64(const uint64_t* __restrict__ w, uint64_t nwords, uint64_t pos) {
+  uint64_t i = pos >> 6;
+  uint32_t sh = (uint32_t)(pos & 63);
+  uint64_t a = i < nwords ? __ldg(w + i) : 0ull;
+  if (!sh) return a;
+  uint64_t b = i + 1 < nwords ? __ldg(w + i + 1) : 0ull;
+  return (a >> sh) | (b << (64 - sh));
+}
+
+__device__ __forceinline__ uint64_t low_mask64(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1); }
+
+// Bits emitted for one plane (R11) given its plane word W (bit r = bit of the
+// r-th coded coefficient) and n coefficients already significant:
+// n verbatim bits, then (if n < N) one test bit per newly significant
+// coefficient, the run of coefficient bits up to and including it, and a
+// closing 0 test bit unless the last coefficient became significant.
+template <int N>
+__device__ __forceinline__ int plane_len(uint64_t W, int n) {
+  if (n >= N) return n;
+  uint64_t rest = n >= 64 ? 0ull : (W >> n);
+  if (!rest) return n + 1;
+  int hi = 64 - __clzll((long long)W);  // one past the highest set position
+  int m = __popcll((long long)rest);
+  return n + m + (hi - n) + (hi < N ? 1 : 0);
+}
+
+}  // namespace pcz

@@ -1,0 +1,77 @@
+// pcz_kernels.h -- parameter blocks and launchers shared between the C-ABI
+// host code (pcz_api.cu) and the kernels.  Internal to libpcz.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pcz {
+
+constexpr int kMaxComponents = 64;
+constexpr int kChunk = 32;  // bricks per index chunk (R15)
+
+// Launch parameters of the fused construction kernel (Algorithm 1 over every
+// brick of a field, all components in one pass).
+struct CompressParams {
+  const void* field;             // device, prod(dims) values of T
+  int64_t dims[3];               // extents, x fastest (1 beyond ndims)
+  int64_t nb[3];                 // bricks per axis
+  int64_t nbricks, nchunks;
+  int n;                         // components
+  uint64_t tau_bits[kMaxComponents];  // bit pattern of the largest T not above tau_i
+  int L[kMaxComponents];              // floor(log2(tau_i))
+  uint64_t* pool;                // scratch for the chunks' bits, pool_words u64 words
+  uint64_t pool_words;
+  unsigned long long* pool_used; // bump counter (words)
+  uint32_t* chunk_nwords;        // [n][nchunks] u64 words of each chunk
+  uint64_t* chunk_pool;          // [n][nchunks] word offset of each chunk in the pool
+  uint16_t* brick_len;           // [n][nbricks] bits of each brick
+  uint32_t* chunk_counts;        // [n][nchunks][5] ZERO, CODED, RAW, escalations, Eq. 1 failures
+  unsigned int* flags;           // bit 0 non-finite input, bit 1 pool too small
+};
+
+// One component's stream as the retrieval kernel sees it.
+struct CompDesc {
+  const uint64_t* payload;
+  uint64_t nwords;
+  const uint64_t* chunk_word;    // [nchunks] first payload word of each chunk
+  const uint16_t* brick_len;     // [nbricks]
+  int L;                         // floor(log2(tau_i))
+  int pad_;
+};
+
+// Launch parameters of the retrieval kernel (Algorithm 2 on the bricks that
+// meet a box, components k0+1..k).
+struct RetrieveParams {
+  const CompDesc* comp;          // device array of n descriptors
+  int64_t dims[3], nb[3], nbricks, nchunks;
+  int k0, k;
+  int64_t lo[3], hi[3];          // box, element units, half-open
+  int64_t bl[3], bn[3];          // first brick and brick counts of the box
+  int64_t nbox;                  // bricks meeting the box
+  void* out;                     // box values of T (read too when k0 > 0)
+  int write;                     // 0: parse and check only
+  unsigned int* err;             // bit 0: a stream failed to parse
+};
+
+enum { kFlagNonFinite = 1u, kFlagPoolOverflow = 2u };
+
+// Launchers (each returns the launch error).
+cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaStream_t s);
+cudaError_t launch_retrieve(int dtype, int ndims, const RetrieveParams& p, cudaStream_t s);
+cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint64_t* totals,
+                               const uint32_t* chunk_counts, unsigned long long* counts, int n,
+                               int64_t nchunks, cudaStream_t s);
+cudaError_t launch_pack(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
+                        const uint64_t* word_off, const uint64_t* comp_base, uint64_t* payload, int n,
+                        int64_t nchunks, cudaStream_t s);
+cudaError_t launch_range(int dtype, const void* x, int64_t count, unsigned long long* enc, unsigned int* flags,
+                         cudaStream_t s);
+
+// Dynamic shared memory and block shape of the kernels (host-side queries).
+int compress_block_threads(int ndims);
+size_t compress_smem_bytes(int dtype, int ndims);
+int retrieve_block_threads(int ndims);
+int retrieve_bricks_per_block(int ndims);
+
+}  // namespace pcz

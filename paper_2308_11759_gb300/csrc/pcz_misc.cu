@@ -1,0 +1,176 @@
+// pcz_misc.cu -- the memory-bound kernels around the fused coder:
+//  * k_scan_chunks: per component, exclusive prefix sum of the chunks' word
+//    counts (their place in the packed stream) and the component totals, plus
+//    the block-mode counters;
+//  * k_pack: copies every chunk from the scratch pool to its place in the
+//    component's stream (word aligned, so a plain copy);
+//  * k_range: min and max of a field (Sec. 5.1: tau_0 is the value range) and
+//    a check that every value is finite.
+#include <cstdint>
+
+#include "pcz_device.cuh"
+#include "pcz_kernels.h"
+
+namespace pcz {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+
+// One CTA per component; tiles of 4096 chunks with a block-wide scan and a
+// running carry.
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __restrict__ nwords,
+                                                               uint64_t* __restrict__ word_off,
+                                                               uint64_t* __restrict__ totals,
+                                                               const uint32_t* __restrict__ chunk_counts,
+                                                               unsigned long long* __restrict__ counts,
+                                                               int64_t nchunks) {
+  __shared__ uint64_t warp_sums[32];
+  __shared__ uint64_t carry_s;
+  __shared__ unsigned long long cnt_s[5];
+  const int comp = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t* in = nwords + (int64_t)comp * nchunks;
+  uint64_t* out = word_off + (int64_t)comp * nchunks;
+  const uint32_t* cc = chunk_counts + (int64_t)comp * nchunks * 5;
+  if (tid == 0) carry_s = 0;
+  if (tid < 5) cnt_s[tid] = 0;
+  unsigned long long my_cnt[5] = {0, 0, 0, 0, 0};
+  __syncthreads();
+  for (int64_t tile = 0; tile < nchunks; tile += (int64_t)kScanThreads * kScanItems) {
+    const int64_t first = tile + (int64_t)tid * kScanItems;
+    uint64_t v[kScanItems];
+    uint64_t local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+      const int64_t c = first + q;
+      v[q] = c < nchunks ? in[c] : 0u;
+      local += v[q];
+      if (c < nchunks) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) my_cnt[k] += cc[c * 5 + k];
+      }
+    }
+    uint64_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t ws = warp_sums[lane];
+      uint64_t wi = ws;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      warp_sums[lane] = wi - ws;  // exclusive over warps
+    }
+    __syncthreads();
+    uint64_t run = carry_s + warp_sums[warp] + (incl - local);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+      const int64_t c = first + q;
+      if (c < nchunks) out[c] = run;
+      run += v[q];
+    }
+    __syncthreads();
+    if (tid == kScanThreads - 1) carry_s = run;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) atomicAdd(&cnt_s[k], my_cnt[k]);
+  __syncthreads();
+  if (tid == 0) totals[comp] = carry_s;
+  if (tid < 5) counts[comp * 5 + tid] = cnt_s[tid];
+}
+
+// One warp per (component, chunk): word-aligned copy from the pool.
+__global__ void __launch_bounds__(256) k_pack(const uint64_t* __restrict__ pool, const uint32_t* __restrict__ nwords,
+                                              const uint64_t* __restrict__ chunk_pool,
+                                              const uint64_t* __restrict__ word_off,
+                                              const uint64_t* __restrict__ comp_base, uint64_t* __restrict__ payload,
+                                              int n, int64_t nchunks) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < (int64_t)n * nchunks;
+       wi += warps) {
+    const int comp = (int)(wi / nchunks);
+    const uint32_t nw = nwords[wi];
+    const uint64_t* src = pool + chunk_pool[wi];
+    uint64_t* dst = payload + comp_base[comp] + word_off[wi];
+    for (uint32_t w = lane; w < nw; w += 32) dst[w] = src[w];
+  }
+}
+
+// Order-preserving map of a finite T to an unsigned integer.
+template <typename T>
+__device__ __forceinline__ unsigned long long order_key(T v) {
+  using F = Fmt<T>;
+  const typename F::U b = F::bits(v);
+  const typename F::U k = (b & F::SIGN) ? (typename F::U)~b : (typename F::U)(b | F::SIGN);
+  return (unsigned long long)k;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, int64_t count,
+                                               unsigned long long* __restrict__ enc, unsigned int* __restrict__ flags) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const T v = x[i];
+    if (not_finite<T>(v)) {
+      bad = true;
+      continue;
+    }
+    const unsigned long long k = order_key<T>(v);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o), c = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = c > hi ? c : hi;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagNonFinite);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(enc, lo);
+    atomicMax(enc + 1, hi);
+  }
+}
+
+cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint64_t* totals,
+                               const uint32_t* chunk_counts, unsigned long long* counts, int n, int64_t nchunks,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_scan_chunks<<<n, kScanThreads, 0, s>>>(nwords, word_off, totals, chunk_counts, counts, nchunks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
+                        const uint64_t* word_off, const uint64_t* comp_base, uint64_t* payload, int n,
+                        int64_t nchunks, cudaStream_t s) {
+  const int64_t items = (int64_t)n * nchunks;
+  if (items == 0) return cudaSuccess;
+  int64_t blocks = (items + 7) / 8;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_pack<<<(unsigned)blocks, 256, 0, s>>>(pool, nwords, chunk_pool, word_off, comp_base, payload, n, nchunks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range(int dtype, const void* x, int64_t count, unsigned long long* enc, unsigned int* flags,
+                         cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (dtype == 1)
+    k_range<float><<<(unsigned)blocks, 256, 0, s>>>((const float*)x, count, enc, flags);
+  else
+    k_range<double><<<(unsigned)blocks, 256, 0, s>>>((const double*)x, count, enc, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace pcz

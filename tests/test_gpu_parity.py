@@ -1,0 +1,114 @@
+"""GPU path vs the CPU oracle, through the C ABI: the component streams (payload,
+index, block counters) and every reconstruction must be bit-identical, at
+sizes that span many chunks and ragged edges."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth_fields as S
+from tests.gpu_helpers import parse_serialized
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2308_11759_gb300 as pcz
+
+    pcz.lib()
+    return pcz
+
+
+CASES = [
+    ("gauss64_f64_delta4", lambda: S.gaussians((64, 64, 64), seed=1), "bin4", 4),
+    ("gauss64_f32_delta4", lambda: S.gaussians((64, 64, 64), seed=1, dtype=np.float32), "bin4", 4),
+    ("pl_f32_ragged_decade", lambda: S.powerlaw((45, 38, 33), seed=2, dtype=np.float32), "dec", 8),
+    ("pl_f64_ragged_decade", lambda: S.powerlaw((45, 38, 33), seed=2, dtype=np.float64), "dec", 8),
+    ("fronts_f64_12", lambda: S.fronts((28, 24, 21), seed=5), "dec", 12),
+    ("fronts_f32_12", lambda: S.fronts((28, 24, 21), seed=5, dtype=np.float32), "dec", 12),
+    ("lossless_f64_14", lambda: (10.0 + 4.0 * S.powerlaw((12, 10, 9), seed=21, dtype=np.float64)), "bin4", 14),
+    ("tiny_1x1x1", lambda: np.array([[[3.25]]]), None, 3),
+    ("thin_3x5x130_f32", lambda: S.powerlaw((3, 5, 130), seed=9, dtype=np.float32), "bin4", 5),
+    ("constant", lambda: np.full((9, 8, 7), 1.5), None, 3),
+    ("zeros", lambda: np.zeros((8, 8, 8), dtype=np.float32), None, 2),
+]
+
+
+def _tau(x, kind, n):
+    if kind is None:
+        return [1.0 / (i + 1) for i in range(n)]
+    r = O.value_range(x)
+    return O.tau_binary(r, 4, n) if kind == "bin4" else O.tau_decade(r, n)
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def pair(request, P):
+    _, make, kind, n = request.param
+    x = np.ascontiguousarray(make())
+    tau = _tau(x, kind, n)
+    xd = torch.from_numpy(x).cuda()
+    if kind is not None:  # the product's own schedule from the device range is the oracle's, bit for bit
+        r = P.value_range(xd)
+        gt = P.tau_binary(r, 4, n) if kind == "bin4" else P.tau_decade(r, n)
+        assert gt == tau
+    gpu = P.compress(xd, tau)
+    ref = O.Streams(x, tau, nthreads=4)
+    return x, tau, gpu, ref
+
+
+def test_streams_bitwise(pair):
+    x, tau, gpu, ref = pair
+    d = parse_serialized(gpu.serialize())
+    assert d["n"] == ref.n and d["nbricks"] == ref.nbricks and d["nchunks"] == ref.nchunks
+    for i in range(ref.n):
+        c = d["comps"][i]
+        assert c["tau"] == tau[i]
+        assert np.array_equal(c["brick_len"], ref.brick_len(i)), f"brick lengths of component {i + 1}"
+        assert np.array_equal(c["chunk_word"], ref.chunk_word(i)), f"chunk offsets of component {i + 1}"
+        assert np.array_equal(c["payload"], ref.payload(i)), f"payload of component {i + 1}"
+        assert c["counts"] == [int(v) for v in ref.stats(i)]
+        assert gpu.counts(i)[4] == 0  # Eq. 1 held everywhere
+
+
+def test_retrieve_bitwise_and_eq1(pair):
+    x, tau, gpu, ref = pair
+    for k in range(0, ref.n + 1):
+        got = gpu.retrieve(k=k).cpu().numpy()
+        want = ref.retrieve(k)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), f"k={k}"
+        if k:
+            err = float(np.max(np.abs(np.subtract(x, got, dtype=x.dtype))))
+            assert err <= tau[k - 1]
+
+
+def test_refine_equals_one_shot(pair):
+    x, tau, gpu, ref = pair
+    for k0 in range(0, ref.n):
+        acc = gpu.retrieve(k=k0)
+        for k in range(k0 + 1, ref.n + 1):
+            gpu.refine(k - 1, k, acc)
+            assert torch.equal(acc.view(torch.uint8), gpu.retrieve(k=k).view(torch.uint8))
+
+
+def test_subbox(pair):
+    x, tau, gpu, ref = pair
+    rng = np.random.default_rng(3)
+    k = (ref.n + 1) // 2
+    full = gpu.retrieve(k=k).cpu().numpy()
+    for _ in range(6):
+        lo = [int(rng.integers(0, s)) for s in x.shape]
+        hi = [int(rng.integers(l + 1, s + 1)) for l, s in zip(lo, x.shape)]
+        part = gpu.retrieve(k=k, box=(lo, hi)).cpu().numpy()
+        sl = tuple(slice(l, h) for l, h in zip(lo, hi))
+        assert np.array_equal(part, full[sl])
+        assert np.array_equal(part, ref.retrieve(k, box=(lo, hi)))
+
+
+def test_query_by_tolerance(pair):
+    x, tau, gpu, ref = pair
+    for i, t in enumerate(tau):
+        assert gpu.query_k(t) == i + 1
+        got = gpu.retrieve(tau=t * 1.5).cpu().numpy()
+        assert np.array_equal(got, ref.retrieve(O.query_k(tau, t * 1.5)))
