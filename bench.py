@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-component progressive compression and retrieval path.
+
+Workload (the large plain-method configuration): a 512^3 random-phase Gaussian
+field with a k^-5/3 power spectrum, in float32 and in float64, compressed into
+8 components with tau_i = 10^-(i+1) * range (i = 1..8), then retrieved at every
+k = 1..8 (Algorithm 1 once, Algorithm 2 for each k).  One step = for each dtype:
+range reduction -> tolerance schedule -> compress -> 8 queries + retrievals.
+
+`value` is raw field bytes processed per second over the whole step (each
+compress and each retrieval counts the field's bytes once), with the fields
+resident in HBM when timing starts; both fields exceed the 129 MB L2, so no
+flush is needed between steps.  `e2e` is the same metric through the same
+calls with host (pinned) buffers: the field is copied in by pc_compress and
+every retrieval is written back to host memory.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pcz|reference]
+
+With --impl reference the CPU oracle (the test-infrastructure implementation
+of the same method) is timed on a bounded sample of the same workload.  For
+N > 1 (torchrun) every rank runs its own replica: the method has no data-path
+exchange (bricks are independent), so there is no collective beyond the
+timing barrier.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_COMP = 8
+WORKLOAD = ("512^3 random-phase Gaussian field (P(k) ~ k^-5/3, unit variance), float32 and float64, "
+            "8 components, tau_i = 1e-(i+1) * range, compress then retrieval at every k = 1..8")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.lines = []
+        self.proc = None
+        self.bus_id = bus_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def make_fields(size, device):
+    import torch
+
+    import synth_fields as S
+
+    f64 = S.powerlaw((size, size, size), seed=2, dtype=np.float64, device=device)
+    f32 = f64.to(torch.float32)
+    torch.cuda.synchronize()
+    return {"f32": f32.contiguous(), "f64": f64.contiguous()}
+
+
+def algorithmic_bytes(st, field_bytes):
+    """Bytes the method must move: compress = read x + write every component's
+    payload and index; retrieval at k = read components 1..k + write x~."""
+    comp_payload = []
+    idx = 0
+    for i in range(st.n):
+        _, bits, ib = st.info(i)
+        comp_payload.append(bits // 8)
+        idx = ib
+    compress = field_bytes + sum(comp_payload) + st.n * idx
+    retrieve = [sum(comp_payload[:k]) + k * idx + field_bytes for k in range(1, st.n + 1)]
+    return compress, retrieve, comp_payload
+
+
+def run_pcz(args, rank, world, device):
+    import torch
+
+    import paper_2308_11759_gb300 as pcz
+
+    pcz.lib()
+    fields = make_fields(args.size, device)
+    outs = {k: torch.empty_like(v) for k, v in fields.items()}
+    nvox = args.size ** 3
+    held = {}
+
+    def step(host=False, hbufs=None):
+        for name, x in fields.items():
+            if host:  # e2e: the field arrives from pinned host memory
+                x = hbufs[name + "_dev"]
+                x.copy_(hbufs[name], non_blocking=True)
+            lo, hi = pcz.field_range(x)  # a1: tau_0 = range
+            tau = pcz.tau_decade(hi - lo, N_COMP)
+            if name in held:
+                held.pop(name).close()
+            st = pcz.compress(x, tau)  # a2..a9
+            held[name] = st
+            dst = hbufs[name + "_out"] if host else outs[name]
+            for k in range(1, N_COMP + 1):  # a10, a11: query at tau_k, then Algorithm 2
+                kk = st.query_k(tau[k - 1])
+                st.retrieve(k=kk, out=dst)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # sizes and per-component rates of this workload
+    info = {}
+    for name, x in fields.items():
+        st = held[name]
+        fb = x.numel() * x.element_size()
+        cb, rb, pay = algorithmic_bytes(st, fb)
+        info[name] = dict(field_bytes=fb, compress_bytes=cb, retrieve_bytes=rb,
+                          rates=[round(8 * p / nvox, 4) for p in pay],
+                          counts=[st.counts(i) for i in range(st.n)])
+
+    bus = None
+    try:
+        props = torch.cuda.get_device_properties(device)
+        bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    except Exception:
+        pass
+    sampler = ClockSampler(bus)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    pcz.timing_enable(True)
+    sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ktimes = pcz.timing_read()
+    pcz.timing_enable(False)
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    raw_bytes_step = sum(v["field_bytes"] * (1 + N_COMP) for v in info.values())
+    value = world * raw_bytes_step * args.steps / (ms_total * 1e-3) / 1e9
+
+    # roofline of the dominant kernel, from its live CUDA-event durations
+    hbm, peak_kind = peaks()
+    alg = {"compress": sum(v["compress_bytes"] for v in info.values()) * args.steps,
+           "retrieve": sum(sum(v["retrieve_bytes"]) for v in info.values()) * args.steps,
+           "range": sum(v["field_bytes"] for v in info.values()) * args.steps,
+           "pack": 2 * sum(v["compress_bytes"] - v["field_bytes"] for v in info.values()) * args.steps}
+    dom = max(("compress", "retrieve"), key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
+    kernels = {}
+    for k, (ms, n) in ktimes.items():
+        if n:
+            kernels[k] = {"launches": n, "ms_per_launch": round(ms / n, 4), "share": round(ms / ms_total, 4),
+                          "gbs_algorithmic": round(alg[k] / (ms * 1e-3) / 1e9, 1) if k in alg and ms > 0 else None}
+    launches = sum(n for _, n in ktimes.values())
+
+    # e2e: the same step through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hbufs = {}
+        for name, x in fields.items():
+            hbufs[name] = x.cpu().pin_memory()
+            hbufs[name + "_dev"] = torch.empty_like(x)
+            hbufs[name + "_out"] = torch.empty(x.shape, dtype=x.dtype).pin_memory()
+        step(host=True, hbufs=hbufs)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        a = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step(host=True, hbufs=hbufs)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - a
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=device, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = sum(v["field_bytes"] for v in info.values())
+        d2h = sum(v["field_bytes"] * N_COMP for v in info.values())
+        e2e = {"value": round(world * raw_bytes_step * args.steps / (ems * 1e-3) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems / args.steps, 3),
+               "host_wall_s": round(wall, 3)}
+    for st in held.values():
+        st.close()
+    return dict(value=value, ms_step=ms_step, info=info, clocks=clocks, kernels=kernels, launches=launches,
+                roofline={"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+                          "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                          "traffic": None,
+                          "algorithmic_bytes_per_launch": int(alg[dom] / max(dom_n, 1)),
+                          "ms_per_launch": round(dom_ms / max(dom_n, 1), 4)},
+                e2e=e2e, fields=fields)
+
+
+def oracle_sample(fields_np, sub, nthreads):
+    """Times the CPU oracle on a sub^3 corner of each field: Algorithm 1 then
+    Algorithm 2 at every k.  Returns (GB/s of raw bytes, seconds, description)."""
+    import oracle as O
+
+    total_bytes = 0
+    t = time.perf_counter()
+    for name, x in fields_np.items():
+        xs = np.ascontiguousarray(x[:sub, :sub, :sub])
+        tau = O.tau_decade(O.value_range(xs), N_COMP)
+        s = O.Streams(xs, tau, nthreads=nthreads)
+        for k in range(1, N_COMP + 1):
+            s.retrieve(O.query_k(tau, tau[k - 1]))
+        total_bytes += xs.nbytes * (1 + N_COMP)
+    secs = time.perf_counter() - t
+    desc = f"{sub}^3 corner of each field (f32 and f64), compress + retrieval at every k"
+    return total_bytes / secs / 1e9, secs, desc
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pcz", choices=["pcz", "reference"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--sample", type=int, default=128, help="edge of the oracle's sample sub-volume")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_setup()
+    nthreads = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import synth_fields as S
+
+        x64 = S.powerlaw((args.sample, args.sample, args.sample), seed=2, dtype=np.float64)
+        fields_np = {"f32": x64.astype(np.float32), "f64": x64}
+        for _ in range(args.warmup):
+            oracle_sample(fields_np, args.sample, nthreads)
+        vals, secs = [], 0.0
+        for _ in range(args.steps):
+            v, s, desc = oracle_sample(fields_np, args.sample, nthreads)
+            vals.append(v)
+            secs += s
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": "compress/retrieve GB/s vs HBM roofline", "value": round(value, 5),
+                "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(1e3 * secs / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "parallelism": "replicas", "reference_sample": desc},
+                "cpu_baseline": {"value": round(value, 5), "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": round(value, 5), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    r = run_pcz(args, rank, world, device)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fields_np = {k: v[: args.sample, : args.sample, : args.sample].cpu().numpy() for k, v in r["fields"].items()}
+        v, s, desc = oracle_sample(fields_np, args.sample, nthreads)
+        cpu = {"value": round(v, 5), "unit": "GB/s", "cores": nthreads, "kind": "oracle", "sample": desc,
+               "seconds": round(s, 2)}
+    if rank == 0:
+        line = {
+            "metric": "compress/retrieve GB/s vs HBM roofline",
+            "value": round(r["value"], 3),
+            "unit": "GB/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(r["ms_step"], 3),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32,f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "size": args.size, "components": N_COMP,
+                       "inputs_exceed_l2": True, "l2_flush": False, "parallelism": "replicas"},
+            "e2e": r["e2e"],
+            "roofline": r["roofline"],
+            "cpu_baseline": cpu,
+            "clocks": r["clocks"],
+            "gpu_launches": r["launches"],
+            "kernels": r["kernels"],
+            "rates_bits_per_value": {k: v["rates"] for k, v in r["info"].items()},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,25 @@ void pc_streams_free(pc_streams *s);
 pc_status pc_field_range(const void *d_field, int64_t count, pc_dtype dtype, void *cuda_stream, double *vmin,
                          double *vmax);
 
+/*
+ * Kernel timing (instrumentation, off by default).  While enabled, every
+ * kernel the library launches is bracketed by CUDA events recorded on the
+ * stream it is launched on.  pc_timing_read synchronises the device and
+ * returns, per kernel kind, the summed device time in milliseconds and the
+ * number of launches since the last pc_timing_enable; kinds are indexed by
+ * pc_kernel_kind.  ms and launches hold PC_KERNEL_KINDS entries each.
+ */
+typedef enum {
+  PC_KERNEL_COMPRESS = 0, /* fused construction, Algorithm 1 */
+  PC_KERNEL_SCAN = 1,     /* chunk offsets per component */
+  PC_KERNEL_PACK = 2,     /* chunk copy into the streams */
+  PC_KERNEL_RETRIEVE = 3, /* fused reconstruction, Algorithm 2 */
+  PC_KERNEL_RANGE = 4,    /* field min/max */
+  PC_KERNEL_KINDS = 5
+} pc_kernel_kind;
+pc_status pc_timing_enable(int on);
+pc_status pc_timing_read(double *ms, uint64_t *launches);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *pc_last_error(void);
 

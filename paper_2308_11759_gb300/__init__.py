@@ -66,6 +66,10 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int
+        L.pc_timing_enable.argtypes = [C.c_int]
+        L.pc_timing_enable.restype = C.c_int
+        L.pc_timing_read.argtypes = [C.POINTER(C.c_double), u64p]
+        L.pc_timing_read.restype = C.c_int
         L.pc_streams_free.argtypes = [vp]
         L.pc_streams_free.restype = None
         L.pc_last_error.argtypes = []
@@ -268,3 +272,19 @@ def tau_decade(rng: float, n: int, first_exp: int = 2):
     """tau_i = 10^-(first_exp + i - 1) * tau_0 for i = 1..n: each decimal factor
     is the double nearest to it, times the range with one rounding."""
     return [float("1e-%d" % (first_exp + i - 1)) * rng for i in range(1, n + 1)]
+
+
+KERNEL_KINDS = ("compress", "scan", "pack", "retrieve", "range")
+
+
+def timing_enable(on: bool = True):
+    """Start (or stop) per-kernel CUDA-event timing inside the library."""
+    _check(lib().pc_timing_enable(1 if on else 0))
+
+
+def timing_read():
+    """{kernel kind: (total ms, launches)} since timing_enable."""
+    ms = (C.c_double * 5)()
+    n = (C.c_uint64 * 5)()
+    _check(lib().pc_timing_read(ms, n))
+    return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_KINDS)}

@@ -124,6 +124,39 @@ void make_geometry(int ndims, const int64_t* dims, int64_t d3[3], int64_t nb[3],
   *nchunks = (*nbricks + kChunk - 1) / kChunk;
 }
 
+// Optional per-kernel timing: events around each launch, summed on read.
+struct Timing {
+  std::mutex mu;
+  bool on = false;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  double ms[PC_KERNEL_KINDS] = {};
+  uint64_t launches[PC_KERNEL_KINDS] = {};
+} g_timing;
+
+struct TimedLaunch {
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TimedLaunch(int k, cudaStream_t s) : kind(k), st(s) {
+    if (!g_timing.on) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      a = b = nullptr;
+      return;
+    }
+    cudaEventRecord(a, st);
+  }
+  ~TimedLaunch() {
+    if (!a) return;
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    g_timing.pending.push_back({kind, a, b});
+  }
+};
+
 }  // namespace
 
 struct pc_streams {
@@ -217,7 +250,10 @@ pc_status run_retrieve(const pc_streams* s, int k0, int k, const int64_t lo[3], 
     }
     return PC_OK;
   }
-  CK(launch_retrieve(s->dtype, s->ndims, R, st));
+  {
+    TimedLaunch tl(PC_KERNEL_RETRIEVE, st);
+    CK(launch_retrieve(s->dtype, s->ndims, R, st));
+  }
   return PC_OK;
 }
 
@@ -344,9 +380,14 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
       }
       if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 16, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, 16, st);
-      if (e == cudaSuccess) e = launch_compress(dtype, ndims, P, st);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess) {
+        TimedLaunch tl(PC_KERNEL_COMPRESS, st);
+        e = launch_compress(dtype, ndims, P, st);
+      }
+      if (e == cudaSuccess) {
+        TimedLaunch tl(PC_KERNEL_SCAN, st);
         e = launch_scan_chunks(chunk_nwords, s->d_chunk_word, totals, chunk_counts, counts, n, nch, st);
+      }
       if (e == cudaSuccess) e = cudaMemcpyAsync(h_tot.data(), totals, 8 * n, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt.data(), counts, 8 * 5 * n, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, flags, 4, cudaMemcpyDeviceToHost, st);
@@ -373,8 +414,10 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
       }
       e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
       if (e == cudaSuccess) e = cudaMemcpyAsync(comp_base, base.data(), 8 * n, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess) {
+        TimedLaunch tl(PC_KERNEL_PACK, st);
         e = launch_pack(P.pool, chunk_nwords, chunk_pool, s->d_chunk_word, comp_base, s->d_payload, n, nch, st);
+      }
       if (e != cudaSuccess) rc = cuda_fail(e, "pack");
     }
     if (rc == PC_OK) rc = upload_desc(s, st);  // synchronises: scratch is idle when freed
@@ -647,6 +690,45 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
 
 void pc_streams_free(pc_streams* s) { streams_release(s); }
 
+pc_status pc_timing_enable(int on) {
+  g_err.clear();
+  CK(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(g_timing.mu);
+  for (auto& p : g_timing.pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_timing.pending.clear();
+  for (int k = 0; k < PC_KERNEL_KINDS; ++k) {
+    g_timing.ms[k] = 0;
+    g_timing.launches[k] = 0;
+  }
+  g_timing.on = on != 0;
+  return PC_OK;
+}
+
+pc_status pc_timing_read(double* ms, uint64_t* launches) {
+  g_err.clear();
+  if (!ms || !launches) return fail(PC_ERR_ARG, "NULL argument");
+  CK(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(g_timing.mu);
+  for (auto& p : g_timing.pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      g_timing.ms[p.kind] += t;
+      g_timing.launches[p.kind] += 1;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_timing.pending.clear();
+  for (int k = 0; k < PC_KERNEL_KINDS; ++k) {
+    ms[k] = g_timing.ms[k];
+    launches[k] = g_timing.launches[k];
+  }
+  return PC_OK;
+}
+
 pc_status pc_field_range(const void* d_field, int64_t count, pc_dtype dtype, void* cuda_stream, double* vmin,
                          double* vmax) {
   g_err.clear();
@@ -660,7 +742,10 @@ pc_status pc_field_range(const void* d_field, int64_t count, pc_dtype dtype, voi
   unsigned int* flags = (unsigned int*)(enc + 2);
   unsigned long long init[4] = {~0ull, 0ull, 0ull, 0ull};
   CK(cudaMemcpyAsync(enc, init, 32, cudaMemcpyHostToDevice, st));
-  CK(launch_range(dtype, d_field, count, enc, flags, st));
+  {
+    TimedLaunch tl(PC_KERNEL_RANGE, st);
+    CK(launch_range(dtype, d_field, count, enc, flags, st));
+  }
   unsigned long long h[3] = {0, 0, 0};
   CK(cudaMemcpyAsync(h, enc, 24, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
