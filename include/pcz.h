@@ -171,6 +171,41 @@ typedef enum {
 pc_status pc_timing_enable(int on);
 pc_status pc_timing_read(double *ms, uint64_t *launches);
 
+/*
+ * pc_compress without device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while
+ * they run -- a host whose own allocator has already reserved the free device
+ * memory (a framework's caching allocator, an application memory pool), or a
+ * latency-critical loop that must avoid cudaMalloc/cudaFree, which can
+ * synchronise the device.  It computes exactly what pc_compress computes
+ * (Algorithm 1, the same streams bit for bit) but takes all its temporary
+ * memory from one fixed 64 MiB device array inside the library, held on every
+ * GPU that loads the library until the process exits, and writes the streams
+ * into buffers the caller provides:
+ *   d_field     device pointer, 3D field of dtype (ndims must be 3).
+ *   d_payload   device, payload_capacity_words u64 words; receives the
+ *               components' payloads back to back (component i starts at word
+ *               h_words[0] + ... + h_words[i-1]).
+ *   d_chunk_word device, n * ceil(bricks / 32) u64: per component, each
+ *               chunk's first word within that component's payload.
+ *   d_brick_len device, n * bricks u16: each brick's bit length.
+ *   h_words     host, n: payload words per component.
+ *   h_counts    host, 5 * n: the counters of pc_stream_counts per component.
+ * Limit: n * ceil(bricks / 32) must not exceed the bound given in the
+ * PC_ERR_ARG message (about 2000 for float64 and 4000 for float32 fields, e.g.
+ * a 64^3 field with up to 15 float64 components); larger inputs are rejected
+ * before any GPU work, and so is a too small payload buffer (its message
+ * gives the words needed).  The library-internal array is shared by all
+ * calls: calls whose work overlaps on the GPU (other streams or threads) race
+ * on it, so the caller must serialise them.  The first call on a device looks
+ * up the array's device address; make that first call before any stream
+ * capture.  Synchronises cuda_stream.  Errors are reported by pc_last_error().
+ */
+pc_status pc_compress_noalloc(const void *d_field, const int64_t *dims, int ndims, pc_dtype dtype,
+                              const double *tau, int n, uint64_t *d_payload, uint64_t payload_capacity_words,
+                              uint64_t *d_chunk_word, uint16_t *d_brick_len, uint64_t *h_words,
+                              uint64_t *h_counts, void *cuda_stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *pc_last_error(void);
 

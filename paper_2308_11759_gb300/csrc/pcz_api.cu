@@ -159,6 +159,8 @@ struct TimedLaunch {
 
 }  // namespace
 
+void pcz::set_last_error(const char* msg) { g_err = msg; }
+
 struct pc_streams {
   int device = 0;
   int ndims = 0;

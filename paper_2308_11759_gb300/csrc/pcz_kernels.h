@@ -68,6 +68,9 @@ cudaError_t launch_pack(const uint64_t* pool, const uint32_t* nwords, const uint
 cudaError_t launch_range(int dtype, const void* x, int64_t count, unsigned long long* enc, unsigned int* flags,
                          cudaStream_t s);
 
+// Sets the message pc_last_error() returns on this thread.
+void set_last_error(const char* msg);
+
 // Dynamic shared memory and block shape of the kernels (host-side queries).
 int compress_block_threads(int ndims);
 size_t compress_smem_bytes(int dtype, int ndims);
