@@ -107,15 +107,19 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
-def make_fields(size, device):
+def make_fields(size, device, dtypes=("f32", "f64")):
     import torch
 
     import synth_fields as S
 
     f64 = S.powerlaw((size, size, size), seed=2, dtype=np.float64, device=device)
-    f32 = f64.to(torch.float32)
+    out = {}
+    if "f32" in dtypes:
+        out["f32"] = f64.to(torch.float32).contiguous()
+    if "f64" in dtypes:
+        out["f64"] = f64.contiguous()
     torch.cuda.synchronize()
-    return {"f32": f32.contiguous(), "f64": f64.contiguous()}
+    return out
 
 
 def algorithmic_bytes(st, field_bytes):
@@ -138,7 +142,7 @@ def run_pcz(args, rank, world, device):
     import paper_2308_11759_gb300 as pcz
 
     pcz.lib()
-    fields = make_fields(args.size, device)
+    fields = make_fields(args.size, device, tuple(args.dtypes.split(",")))
     outs = {k: torch.empty_like(v) for k, v in fields.items()}
     nvox = args.size ** 3
     held = {}
@@ -298,6 +302,7 @@ def main():
     ap.add_argument("--impl", default="pcz", choices=["pcz", "reference"])
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--sample", type=int, default=128, help="edge of the oracle's sample sub-volume")
+    ap.add_argument("--dtypes", default="f32,f64", help="field types in a step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -141,6 +141,20 @@ pc_status pc_stream_device_ptrs(const pc_streams *s, int i, const uint64_t **pay
                                 const uint16_t **brick_len, uint64_t *payload_words, uint64_t *nchunks,
                                 uint64_t *nbricks);
 
+/* Copies component i's index to host memory: h_chunk_word receives nchunks
+ * u64 (each chunk's first payload word), h_brick_len nbricks u16 (each brick's
+ * bit length); either may be NULL.  Synchronises cuda_stream.  Together with
+ * pc_stream_read this gives any single brick's bits (Sec. 6.1: blocks are
+ * decodable one at a time). */
+pc_status pc_stream_read_index(const pc_streams *s, int i, uint64_t *h_chunk_word, uint16_t *h_brick_len,
+                               void *cuda_stream);
+
+/* Copies nwords payload words of component i, starting at word word_off, to
+ * host memory h_out.  PC_ERR_ARG if the range leaves the payload.
+ * Synchronises cuda_stream. */
+pc_status pc_stream_read(const pc_streams *s, int i, uint64_t word_off, uint64_t nwords, uint64_t *h_out,
+                         void *cuda_stream);
+
 /* Releases the streams and their device memory (waits for the device). */
 void pc_streams_free(pc_streams *s);
 

@@ -322,3 +322,9 @@ def tau_decade(rng: float, n: int, first_exp: int = 2):
     """tau_i = 10^-(first_exp + i - 1) * tau_0, i = 1..n, with each decimal
     factor the double nearest to it and one rounded product."""
     return [float("1e-%d" % (first_exp + i - 1)) * rng for i in range(1, n + 1)]
+
+
+def bits_as_int(words, nbits) -> int:
+    """A bit string (bit b = bit b%64 of word b/64) as a Python integer."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))
+    return int.from_bytes(w.tobytes(), "little") & ((1 << int(nbits)) - 1)

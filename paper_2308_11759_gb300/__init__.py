@@ -61,6 +61,8 @@ def lib():
             "pc_streams_deserialize": [vp, C.c_size_t, vp, C.POINTER(vp)],
             "pc_stream_device_ptrs": [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), u64p, u64p, u64p],
             "pc_field_range": [vp, C.c_int64, C.c_int, vp, dp, dp],
+            "pc_stream_read_index": [vp, C.c_int, u64p, C.POINTER(C.c_uint16), vp],
+            "pc_stream_read": [vp, C.c_int, C.c_uint64, C.c_uint64, u64p, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -235,6 +237,33 @@ class Streams:
         _check(lib().pc_refine(self._h, int(k0), int(k), C.byref(b) if b is not None else None, _ptr(inout),
                                _stream_ptr(stream)))
         return inout
+
+    def read_index(self, i: int, stream=None):
+        """(chunk_word[nchunks] u64, brick_len[nbricks] u16) of component i, on the host."""
+        _, _, _, _, nc, nb = self.device_ptrs(i)
+        cw = np.zeros(nc, dtype=np.uint64)
+        bl = np.zeros(nb, dtype=np.uint16)
+        _check(lib().pc_stream_read_index(self._h, i, cw.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                          bl.ctypes.data_as(C.POINTER(C.c_uint16)), _stream_ptr(stream)))
+        return cw, bl
+
+    def read_payload(self, i: int, word_off: int, nwords: int, stream=None) -> np.ndarray:
+        out = np.zeros(max(nwords, 1), dtype=np.uint64)
+        _check(lib().pc_stream_read(self._h, i, int(word_off), int(nwords), out.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                    _stream_ptr(stream)))
+        return out[:nwords]
+
+    def brick_bits(self, i: int, b: int, index=None):
+        """Brick b's bit string in component i as (python int, bit length)."""
+        cw, bl = index if index is not None else self.read_index(i)
+        c = b // 32
+        start = int(cw[c]) * 64 + int(bl[32 * c:b].astype(np.int64).sum())
+        nbits = int(bl[b])
+        w0 = start // 64
+        nw = (start + nbits + 63) // 64 - w0
+        words = self.read_payload(i, w0, nw)
+        v = int.from_bytes(words.tobytes(), "little") >> (start - 64 * w0)
+        return v & ((1 << nbits) - 1), nbits
 
     def serialize(self, stream=None) -> bytes:
         n = C.c_size_t()

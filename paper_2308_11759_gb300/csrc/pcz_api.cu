@@ -690,6 +690,33 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   return PC_OK;
 }
 
+pc_status pc_stream_read_index(const pc_streams* s, int i, uint64_t* h_chunk_word, uint16_t* h_brick_len,
+                               void* cuda_stream) {
+  g_err.clear();
+  if (!s || i < 0 || i >= s->n) return fail(PC_ERR_ARG, "bad streams or component index");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (h_chunk_word)
+    CK(cudaMemcpyAsync(h_chunk_word, s->d_chunk_word + (int64_t)i * s->nchunks, 8 * (size_t)s->nchunks,
+                       cudaMemcpyDeviceToHost, st));
+  if (h_brick_len)
+    CK(cudaMemcpyAsync(h_brick_len, s->d_brick_len + (int64_t)i * s->nbricks, 2 * (size_t)s->nbricks,
+                       cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+pc_status pc_stream_read(const pc_streams* s, int i, uint64_t word_off, uint64_t nwords, uint64_t* h_out,
+                         void* cuda_stream) {
+  g_err.clear();
+  if (!s || i < 0 || i >= s->n || !h_out) return fail(PC_ERR_ARG, "bad arguments");
+  if (word_off > s->words[i] || nwords > s->words[i] - word_off) return fail(PC_ERR_ARG, "range outside the payload");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (nwords)
+    CK(cudaMemcpyAsync(h_out, s->d_payload + s->word_base[i] + word_off, 8 * nwords, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
 void pc_streams_free(pc_streams* s) { streams_release(s); }
 
 pc_status pc_timing_enable(int on) {

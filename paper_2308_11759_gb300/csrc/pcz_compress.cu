@@ -8,12 +8,15 @@
 //
 // Layout: one CTA per index chunk of 32 bricks (R15), 16 warps; a warp codes
 // two bricks, 16 lanes each; lane t of a brick holds the x-line y = t & 3,
-// z = t >> 2.  The y and z lifting passes and the coefficient reorder go
-// through a per-brick shared buffer.  Bit planes are formed with warp ballots
-// and each lane emits one plane (R11); the planes' significance counts and
-// bit offsets come from warp prefix scans.  The chunk's bits are assembled in
-// shared memory and appended to a scratch pool with one atomic per chunk;
-// pcz_misc.cu then scans the chunk sizes and packs the final streams.
+// z = t >> 2, and after the transform the coded coefficients t + 16j.  The y
+// and z lifting passes and the reorder go through a bank-conflict-free brick
+// buffer in shared memory.  Bit planes come from 32x32 bit transposes across
+// the warp, after which lane p owns plane p (and p + 32): each lane emits its
+// plane's bits (R11), with the significance count before the plane and the
+// plane's bit offset from suffix scans over lanes (planes are coded from the
+// top down).  The chunk's bits are assembled in shared memory and appended to
+// a scratch pool with one atomic per chunk; pcz_misc.cu then scans the chunk
+// sizes and packs the final streams.
 #include <climits>
 #include <type_traits>
 
@@ -42,7 +45,7 @@ template <typename T>
 constexpr size_t compress_smem3() {
   using S = typename Fmt<T>::S;
   return (size_t)chunk_buf_words3<T>() * 4      // chunk bit buffer
-         + (size_t)kChunk * 64 * sizeof(S)     // one brick buffer per brick
+         + (size_t)kChunk * 64 * sizeof(S)     // brick buffers, 128 elements per warp
          + 32 * 4 * 5                          // lengths, offsets, modes, escalations, violations
          + 16;                                 // pool base
 }
@@ -59,8 +62,8 @@ __device__ __forceinline__ void write_plane(uint32_t* buf, uint32_t o, uint64_t 
   uint64_t a0 = 0, a1 = 0, a2 = 0;
   int rel = 0;
   for (int it = 0; it < 64 && w; ++it) {  // one pass per set bit
-    int tz = __ffsll((long long)w) - 1;
-    int r1 = rel, r2 = rel + 1 + tz;  // the test bit and the coefficient's 1
+    const int tz = __ffsll((long long)w) - 1;
+    const int r1 = rel, r2 = rel + 1 + tz;  // the test bit and the coefficient's 1
     if (r1 < 64) a0 |= 1ull << r1; else if (r1 < 128) a1 |= 1ull << (r1 - 64); else a2 |= 1ull << (r1 - 128);
     if (r2 < 64) a0 |= 1ull << r2; else if (r2 < 128) a1 |= 1ull << (r2 - 64); else a2 |= 1ull << (r2 - 128);
     rel = r2 + 1;
@@ -69,6 +72,36 @@ __device__ __forceinline__ void write_plane(uint32_t* buf, uint32_t o, uint64_t 
   or_bits(buf, o, a0);
   or_bits(buf, o + 64, a1);
   or_bits(buf, o + 128, a2);
+}
+
+// Suffix scans of one round of 32 planes (lane l = plane base + l, coded in
+// descending order): n before each plane (max of the one-past-highest set
+// position over the planes above) and the plane's bit offset.
+template <int N>
+__device__ __forceinline__ void plane_scan(uint64_t W, bool act, int lane, int& cmax, int& csum, int& n_out,
+                                           int& off_out) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int hi = (act && W) ? 64 - __clzll((long long)W) : 0;
+  int v = hi;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_down_sync(FULL, v, o);
+    if (lane + o < 32) v = max(v, y);
+  }
+  int ex = __shfl_down_sync(FULL, v, 1);
+  if (lane == 31) ex = 0;
+  const int n = max(ex, cmax);
+  const int len = act ? plane_len<N>(W, n) : 0;
+  int sum = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_down_sync(FULL, sum, o);
+    if (lane + o < 32) sum += y;
+  }
+  n_out = n;
+  off_out = sum - len + csum;
+  cmax = max(cmax, __shfl_sync(FULL, v, 0));
+  csum += __shfl_sync(FULL, sum, 0);
 }
 
 template <typename T>
@@ -82,6 +115,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
   constexpr int HDR = 2 + 3 + F::EBITS;    // mode, escalation, block exponent
   constexpr int LEN_RAW = 2 + N * F::P;
   constexpr int BUFW = chunk_buf_words3<T>();
+  constexpr bool WIDE = F::P == 64;
   constexpr unsigned FULL = 0xffffffffu;
 
   extern __shared__ __align__(16) unsigned char smem[];
@@ -107,7 +141,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
   int64_t bx = 0, by = 0, bz = 0;
   if (have) {
     bx = b % P.nb[0];
-    int64_t r = b / P.nb[0];
+    const int64_t r = b / P.nb[0];
     by = r % P.nb[1];
     bz = r / P.nb[1];
   }
@@ -150,11 +184,20 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     xt[m] = T(0);
     e[m] = F::sub(x[m], T(0));
   }
-  S* mybuf = bbuf + slot * 64;
-  int pos_r[4];
+  S* buf = bbuf + warp * 128;
+  // buffer slots of this lane's line in each pass and of its coded coefficients
+  const int xx = t & 3, yq = t >> 2;
+  int ix[4], iy[4], iz[4], ir[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) pos_r[j] = kPerm3.pos[t + 16 * j];
-  const int xx = t & 3, yq = t >> 2;  // lane roles in the y and z passes
+  for (int m = 0; m < 4; ++m) {
+    ix[m] = sidx<T>(m, ly, lz, h);   // x-line of (y = ly, z = lz)
+    iy[m] = sidx<T>(xx, m, yq, h);   // y-line of (x = xx, z = yq)
+    iz[m] = sidx<T>(xx, yq, m, h);   // z-line of (x = xx, y = yq)
+    const int pos = kPerm3.pos[t + 16 * m];
+    ir[m] = sidx<T>(pos & 3, (pos >> 2) & 3, pos >> 4, h);
+  }
+  uint32_t tkeep[5];
+  transpose_masks(lane, tkeep);
 
   for (int i = 0; i < P.n; ++i) {  // line 2
     const U tb = (U)P.tau_bits[i];
@@ -166,13 +209,13 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
 #pragma unroll
       for (int m = 0; m < 4; ++m) e[m] = __shfl_sync(FULL, e[m], srcl);
     }
-    // R5: a brick whose residual meets tau_i on every in-field value is ZERO
+    // R5: a brick whose residual meets tau_i on every in-field value is ZERO.
+    // (Every lane takes part in each vote: a vote behind && or || would be
+    // skipped by one half of the warp and leave the other half waiting.)
     bool small = true;
 #pragma unroll
     for (int m = 0; m < 4; ++m)
       if (line_in && m < nvx && !within<T>(e[m], tb)) small = false;
-    // (every lane takes part in each vote: a vote behind && or || would be
-    // skipped by one half of the warp and leave the other half waiting)
     const unsigned big_votes = __ballot_sync(FULL, !small);
     const bool zero_blk = !have || ((big_votes & HALF) == 0u);
     bool nf = false;
@@ -196,24 +239,24 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     // R7: lifting along x (in the lane), y and z (shared buffer)
     lift_fwd(q[0], q[1], q[2], q[3]);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) mybuf[4 * t + m] = q[m];
+    for (int m = 0; m < 4; ++m) buf[ix[m]] = q[m];
     __syncwarp();
     {
-      S a = mybuf[xx + 16 * yq], bq = mybuf[xx + 4 + 16 * yq], c = mybuf[xx + 8 + 16 * yq], d = mybuf[xx + 12 + 16 * yq];
+      S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
       lift_fwd(a, bq, c, d);
-      mybuf[xx + 16 * yq] = a; mybuf[xx + 4 + 16 * yq] = bq; mybuf[xx + 8 + 16 * yq] = c; mybuf[xx + 12 + 16 * yq] = d;
+      buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
     }
     __syncwarp();
     {
-      S a = mybuf[xx + 4 * yq], bq = mybuf[xx + 4 * yq + 16], c = mybuf[xx + 4 * yq + 32], d = mybuf[xx + 4 * yq + 48];
+      S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
       lift_fwd(a, bq, c, d);
-      mybuf[xx + 4 * yq] = a; mybuf[xx + 4 * yq + 16] = bq; mybuf[xx + 4 * yq + 32] = c; mybuf[xx + 4 * yq + 48] = d;
+      buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
     }
     __syncwarp();
     // R8, R9: coded order, negabinary.  Lane t holds coefficients t + 16j.
     U u[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) u[j] = nb_fwd<T>(mybuf[pos_r[j]]);
+    for (int j = 0; j < 4; ++j) u[j] = nb_fwd<T>(buf[ir[j]]);
     __syncwarp();
 
     // R10, R13: lowest coded plane; lowered until Eq. 1 holds in T
@@ -222,38 +265,41 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     bool done = zero_blk || raw_forced, pass = false;
     T xtc[4], ec[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) { xtc[m] = xt[m]; ec[m] = e[m]; }
+    for (int m = 0; m < 4; ++m) {
+      xtc[m] = xt[m];
+      ec[m] = e[m];
+    }
     for (int round = 0; round < 8; ++round) {  // esc runs 0..7: at most 8 rounds
       const bool active = !done;
       const int pp = min(max(L + s - C - esc, 0), F::P);
       const U keep = pp >= F::P ? U(0) : (U)~((U(1) << pp) - 1);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) mybuf[pos_r[j]] = nb_inv<T>((U)(u[j] & keep));
+      for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>((U)(u[j] & keep));
       __syncwarp();
       {
-        S a = mybuf[xx + 4 * yq], bq = mybuf[xx + 4 * yq + 16], c = mybuf[xx + 4 * yq + 32], d = mybuf[xx + 4 * yq + 48];
+        S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
         lift_inv(a, bq, c, d);
-        mybuf[xx + 4 * yq] = a; mybuf[xx + 4 * yq + 16] = bq; mybuf[xx + 4 * yq + 32] = c; mybuf[xx + 4 * yq + 48] = d;
+        buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
       }
       __syncwarp();
       {
-        S a = mybuf[xx + 16 * yq], bq = mybuf[xx + 4 + 16 * yq], c = mybuf[xx + 8 + 16 * yq], d = mybuf[xx + 12 + 16 * yq];
+        S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
         lift_inv(a, bq, c, d);
-        mybuf[xx + 16 * yq] = a; mybuf[xx + 4 + 16 * yq] = bq; mybuf[xx + 8 + 16 * yq] = c; mybuf[xx + 12 + 16 * yq] = d;
+        buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
       }
       __syncwarp();
       S r[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) r[m] = mybuf[4 * t + m];
+      for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
       __syncwarp();
       lift_inv(r[0], r[1], r[2], r[3]);
       bool ok = true;
       T xtn[4], en[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const T xi = F::val(dequantize_bits<T>(r[m], s));  // line 5: x_i = D(y_i)
-        xtn[m] = F::add(xt[m], xi);                        // line 6 (candidate)
-        en[m] = F::sub(x[m], xtn[m]);                      // the next residual
+        const T xi = dequantize_val<T>(r[m], s);  // line 5: x_i = D(y_i)
+        xtn[m] = F::add(xt[m], xi);               // line 6 (candidate)
+        en[m] = F::sub(x[m], xtn[m]);             // the next residual
         if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
       }
       const bool pass_h = (__ballot_sync(FULL, !ok) & HALF) == 0u;
@@ -263,7 +309,10 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
           done = true;
           p = pp;
 #pragma unroll
-          for (int m = 0; m < 4; ++m) { xtc[m] = xtn[m]; ec[m] = en[m]; }
+          for (int m = 0; m < 4; ++m) {
+            xtc[m] = xtn[m];
+            ec[m] = en[m];
+          }
         } else if (esc == 7 || pp == 0) {
           done = true;
         } else {
@@ -273,69 +322,42 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
       if (__all_sync(FULL, done)) break;
     }
 
-    // R11: plane words of the coded coefficients and the CODED length
-    U orr = u[0] | u[1] | u[2] | u[3];
+    // R11: plane words by transposing the coefficient bits across the warp:
+    // lane l then holds plane l (and l + 32) of both bricks.
+    uint64_t WA0, WB0, WA1 = 0, WB1 = 0;
+    {
+      uint32_t tl[4];
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) orr |= (U)__shfl_xor_sync(FULL, orr, o);
-    const int top = orr ? (F::P - 1 - F::clz(orr)) : -1;
-    const int K = (pass && top >= p) ? top - p + 1 : 0;          // planes from top down to p
-    const int Z = pass ? (F::P - 1 - max(top, p - 1)) : 0;       // empty planes above: one bit each
-    const int KA = __shfl_sync(FULL, K, 0), KB = __shfl_sync(FULL, K, 16);
-    const int topA = __shfl_sync(FULL, top, 0), topB = __shfl_sync(FULL, top, 16);
-    uint64_t WA0 = 0, WA1 = 0, WB0 = 0, WB1 = 0;
-    if (KA > 0 || KB > 0) {
-      const int phi = max(KA ? topA : -1, KB ? topB : -1);
-      const int plo = min(KA ? topA - KA + 1 : INT_MAX, KB ? topB - KB + 1 : INT_MAX);
-      for (int pl = phi; pl >= plo; --pl) {
-        const unsigned b0 = __ballot_sync(FULL, (unsigned)(u[0] >> pl) & 1u);
-        const unsigned b1 = __ballot_sync(FULL, (unsigned)(u[1] >> pl) & 1u);
-        const unsigned b2 = __ballot_sync(FULL, (unsigned)(u[2] >> pl) & 1u);
-        const unsigned b3 = __ballot_sync(FULL, (unsigned)(u[3] >> pl) & 1u);
-        const uint64_t wa = (uint64_t)__byte_perm(b0, b1, 0x5410) | ((uint64_t)__byte_perm(b2, b3, 0x5410) << 32);
-        const uint64_t wb = (uint64_t)__byte_perm(b0, b1, 0x7632) | ((uint64_t)__byte_perm(b2, b3, 0x7632) << 32);
-        const int ka = topA - pl, kb = topB - pl;
-        if (ka >= 0 && ka < KA && (ka & 31) == lane) { if (ka >> 5) WA1 = wa; else WA0 = wa; }
-        if (kb >= 0 && kb < KB && (kb & 31) == lane) { if (kb >> 5) WB1 = wb; else WB0 = wb; }
+      for (int j = 0; j < 4; ++j) tl[j] = transpose32((uint32_t)u[j], lane, tkeep);
+      WA0 = (uint64_t)__byte_perm(tl[0], tl[1], 0x5410) | ((uint64_t)__byte_perm(tl[2], tl[3], 0x5410) << 32);
+      WB0 = (uint64_t)__byte_perm(tl[0], tl[1], 0x7632) | ((uint64_t)__byte_perm(tl[2], tl[3], 0x7632) << 32);
+      if constexpr (WIDE) {
+        uint32_t th[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) th[j] = transpose32((uint32_t)((uint64_t)u[j] >> 32), lane, tkeep);
+        WA1 = (uint64_t)__byte_perm(th[0], th[1], 0x5410) | ((uint64_t)__byte_perm(th[2], th[3], 0x5410) << 32);
+        WB1 = (uint64_t)__byte_perm(th[0], th[1], 0x7632) | ((uint64_t)__byte_perm(th[2], th[3], 0x7632) << 32);
       }
     }
-    // per brick: n before each plane (prefix max) and its bit offset (prefix sum)
-    int nA0 = 0, nA1 = 0, nB0 = 0, nB1 = 0, oA0 = 0, oA1 = 0, oB0 = 0, oB1 = 0, totA = 0, totB = 0;
-#pragma unroll
-    for (int hb = 0; hb < 2; ++hb) {
-      const int KX = hb ? KB : KA;
+    const int pA = __shfl_sync(FULL, p, 0), pB = __shfl_sync(FULL, p, 16);
+    const bool passA = __shfl_sync(FULL, (int)pass, 0) != 0, passB = __shfl_sync(FULL, (int)pass, 16) != 0;
+    // planes P-1 .. p are coded, from the top: the high round (planes 32 + l)
+    // first for 64-bit coefficients, then planes l
+    int nA0 = 0, nA1 = 0, nB0 = 0, nB1 = 0, oA0 = 0, oA1 = 0, oB0 = 0, oB1 = 0;
+    int totA = 0, totB = 0;
+    {
       int cmax = 0, csum = 0;
-#pragma unroll
-      for (int rd = 0; rd < 2; ++rd) {
-        if (rd == 1 && KX <= 32) break;
-        const int k = lane + 32 * rd;
-        const uint64_t W = hb ? (rd ? WB1 : WB0) : (rd ? WA1 : WA0);
-        const bool act = k < KX;
-        const int hi = (act && W) ? 64 - __clzll((long long)W) : 0;
-        int v = hi;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(FULL, v, o);
-          if (lane >= o) v = max(v, y);
-        }
-        int ex = __shfl_up_sync(FULL, v, 1);
-        if (lane == 0) ex = 0;
-        const int nn = max(ex, cmax);
-        const int len = act ? plane_len<N>(W, nn) : 0;
-        int sum = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(FULL, sum, o);
-          if (lane >= o) sum += y;
-        }
-        const int off = sum - len + csum;
-        if (hb) { if (rd) { nB1 = nn; oB1 = off; } else { nB0 = nn; oB0 = off; } }
-        else { if (rd) { nA1 = nn; oA1 = off; } else { nA0 = nn; oA0 = off; } }
-        cmax = max(cmax, __shfl_sync(FULL, v, 31));
-        csum += __shfl_sync(FULL, sum, 31);
-      }
-      if (hb) totB = csum; else totA = csum;
+      if constexpr (WIDE) plane_scan<N>(WA1, passA && lane + 32 >= pA, lane, cmax, csum, nA1, oA1);
+      plane_scan<N>(WA0, passA && lane >= pA, lane, cmax, csum, nA0, oA0);
+      totA = csum;
     }
-    const int lenC = HDR + Z + (h ? totB : totA);
+    {
+      int cmax = 0, csum = 0;
+      if constexpr (WIDE) plane_scan<N>(WB1, passB && lane + 32 >= pB, lane, cmax, csum, nB1, oB1);
+      plane_scan<N>(WB0, passB && lane >= pB, lane, cmax, csum, nB0, oB0);
+      totB = csum;
+    }
+    const int lenC = HDR + (h ? totB : totA);
 
     // R14: RAW replaces a longer CODED brick only if it also meets tau_i
     bool raw_ok = false;
@@ -351,23 +373,24 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     const int mode = zero_blk ? kModeZero : (pass && !(lenC > LEN_RAW && raw_ok)) ? kModeCoded : kModeRaw;
     const int blen = !have ? 0 : mode == kModeZero ? 2 : mode == kModeRaw ? LEN_RAW : lenC;
 
-    // line 6: commit x~_i and the next residual; keep e_i for a RAW brick
-    T e_raw[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      e_raw[m] = e[m];
-      if (mode == kModeCoded) {
-        xt[m] = xtc[m];
-        e[m] = ec[m];
-      } else if (mode == kModeRaw) {
-        xt[m] = F::add(xt[m], e_raw[m]);
-        e[m] = F::sub(x[m], xt[m]);
-      }
-    }
+    // line 6: x~_i and the next residual, committed after the bits are written
+    // (a RAW brick stores the current residual)
+    T xtnew[4], enew[4];
     int viol = 0;  // Eq. 1 failures left (only a RAW brick can have them)
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
-      if (line_in && m < nvx && !within<T>(e[m], tb)) ++viol;
+    for (int m = 0; m < 4; ++m) {
+      if (mode == kModeCoded) {
+        xtnew[m] = xtc[m];
+        enew[m] = ec[m];
+      } else if (mode == kModeRaw) {
+        xtnew[m] = F::add(xt[m], e[m]);
+        enew[m] = F::sub(x[m], xtnew[m]);
+      } else {
+        xtnew[m] = xt[m];
+        enew[m] = e[m];
+      }
+      if (line_in && m < nvx && !within<T>(enew[m], tb)) ++viol;
+    }
 #pragma unroll
     for (int o = 8; o >= 1; o >>= 1) viol += __shfl_xor_sync(FULL, viol, o);
 
@@ -421,27 +444,31 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     }
     __syncthreads();
 
-    // write this component's bits of the two bricks into the chunk buffer
+    // this component's bits of the warp's two bricks, into the chunk buffer
     const uint32_t boff = (uint32_t)s_off[slot];
     if (have && mode == kModeRaw) {
       if (t == 0) or_bits(cbuf, boff, (uint64_t)kModeRaw);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) or_bits(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(e_raw[m]));
+      for (int m = 0; m < 4; ++m) or_bits(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(e[m]));
     } else if (have && mode == kModeCoded && t == 0) {
       or_bits(cbuf, boff, (uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5));
     }
     const int modeA = __shfl_sync(FULL, mode, 0), modeB = __shfl_sync(FULL, mode, 16);
-    const int ZA = __shfl_sync(FULL, Z, 0), ZB = __shfl_sync(FULL, Z, 16);
     const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
     if (haveA && modeA == kModeCoded) {
-      const uint32_t base = (uint32_t)s_off[warp * 2] + HDR + ZA;
-      if (lane < KA) write_plane<N>(cbuf, base + oA0, WA0, nA0);
-      if (lane + 32 < KA) write_plane<N>(cbuf, base + oA1, WA1, nA1);
+      const uint32_t base = (uint32_t)s_off[warp * 2] + HDR;
+      if (lane >= pA) write_plane<N>(cbuf, base + oA0, WA0, nA0);
+      if (WIDE && lane + 32 >= pA) write_plane<N>(cbuf, base + oA1, WA1, nA1);
     }
     if (haveB && modeB == kModeCoded) {
-      const uint32_t base = (uint32_t)s_off[warp * 2 + 1] + HDR + ZB;
-      if (lane < KB) write_plane<N>(cbuf, base + oB0, WB0, nB0);
-      if (lane + 32 < KB) write_plane<N>(cbuf, base + oB1, WB1, nB1);
+      const uint32_t base = (uint32_t)s_off[warp * 2 + 1] + HDR;
+      if (lane >= pB) write_plane<N>(cbuf, base + oB0, WB0, nB0);
+      if (WIDE && lane + 32 >= pB) write_plane<N>(cbuf, base + oB1, WB1, nB1);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      xt[m] = xtnew[m];
+      e[m] = enew[m];
     }
     __syncthreads();
     {  // append the chunk to the pool and clear the buffer for the next component

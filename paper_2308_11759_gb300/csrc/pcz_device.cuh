@@ -211,6 +211,27 @@ __device__ __forceinline__ typename Fmt<T>::U dequantize_bits(typename Fmt<T>::S
   return q < 0 ? (out | F::SIGN) : out;
 }
 
+// R13 for float fields, the common case in a few instructions: when 2^-s is a
+// normal float and the result is normal or overflows, int->float rounding
+// followed by an exact power-of-two scaling is the single correct rounding.
+// Other cases take the general path.
+__device__ __forceinline__ float dequantize_f32(int32_t q, int s) {
+  if (q == 0) return 0.0f;
+  const uint32_t a = q < 0 ? 0u - (uint32_t)q : (uint32_t)q;
+  const int nb = 32 - __clz(a);
+  if (s >= -127 && s <= 126 && nb - s >= -125)
+    return __fmul_rn(__int2float_rn(q), __uint_as_float((uint32_t)(127 - s) << 23));
+  return __uint_as_float(dequantize_bits<float>(q, s));
+}
+
+template <typename T>
+__device__ __forceinline__ T dequantize_val(typename Fmt<T>::S q, int s) {
+  if constexpr (sizeof(T) == 4)
+    return dequantize_f32(q, s);
+  else
+    return Fmt<T>::val(dequantize_bits<T>(q, s));
+}
+
 // |e| <= tau on bit patterns: tb is the pattern of the largest T value not
 // above tau, so the comparison is exact; NaN and +-inf fail it.
 template <typename T>
@@ -273,6 +294,73 @@ __device__ __forceinline__ uint64_t peek64(const uint64_t* __restrict__ w, uint6
 }
 
 __device__ __forceinline__ uint64_t low_mask64(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1); }
+
+// ---------------------------------------------------------------------------
+// 32x32 bit-matrix transpose across a warp: lane l holds row l; afterwards
+// lane l holds column l (bit r = bit l of row r).  Five exchange stages; keep
+// holds this lane's per-stage masks from transpose_masks().
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void transpose_masks(int lane, uint32_t keep[5]) {
+  const uint32_t lo[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int k = 16 >> st;
+    keep[st] = (lane & k) ? ~lo[st] : lo[st];
+  }
+}
+
+__device__ __forceinline__ uint32_t transpose32(uint32_t a, int lane, const uint32_t keep[5]) {
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int k = 16 >> st;
+    const uint32_t b = __shfl_xor_sync(0xffffffffu, a, k);
+    const uint32_t moved = (lane & k) ? (b >> k) : (b << k);
+    a = (a & keep[st]) | (moved & ~keep[st]);
+  }
+  return a;
+}
+
+// Index of brick element (x, y, z) of the warp's half h in the shared brick
+// buffer (two bricks, 128 elements).  The rotations make every lifting pass
+// (16 lanes of a brick reading one line position each) and the x-line
+// accesses free of bank conflicts for 4- and 8-byte elements.
+template <typename T>
+__device__ __forceinline__ int sidx(int x, int y, int z, int h) {
+  if constexpr (sizeof(T) == 8)
+    return 64 * h + 16 * z + 4 * ((y + z) & 3) + ((x + z) & 3);
+  else
+    return 32 * z + 16 * h + 4 * ((y + z) & 3) + ((x + z) & 3);
+}
+
+// Sequential bit reader over a word stream with the two current words in
+// registers: one load per 64 bits consumed.  Positions must not decrease.
+struct BitReader {
+  const uint64_t* __restrict__ w;
+  uint64_t nw, wi, a, b;
+  __device__ __forceinline__ uint64_t ld(uint64_t i) const { return i < nw ? __ldg(w + i) : 0ull; }
+  __device__ __forceinline__ void init(const uint64_t* words, uint64_t nwords, uint64_t pos) {
+    w = words;
+    nw = nwords;
+    wi = pos >> 6;
+    a = ld(wi);
+    b = ld(wi + 1);
+  }
+  __device__ __forceinline__ uint64_t peek(uint64_t pos) {
+    const uint64_t i = pos >> 6;
+    if (i != wi) {
+      if (i == wi + 1) {
+        a = b;
+        b = ld(i + 1);
+      } else {
+        a = ld(i);
+        b = ld(i + 1);
+      }
+      wi = i;
+    }
+    const uint32_t sh = (uint32_t)(pos & 63);
+    return sh ? (a >> sh) | (b << (64 - sh)) : a;
+  }
+};
 
 // Bits emitted for one plane (R11) given its plane word W (bit r = bit of the
 // r-th coded coefficient) and n coefficients already significant:

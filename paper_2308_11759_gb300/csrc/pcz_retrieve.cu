@@ -7,12 +7,16 @@
 // bricks meeting the box are touched: zfp-style blocks decode on their own
 // (Sec. 6.1).
 //
-// Layout: 4 warps per CTA, two bricks per warp, 16 lanes per brick, lane t
-// holding the x-line y = t & 3, z = t >> 2.  Parsing a component's bit planes
-// is sequential (each plane's length depends on the planes before it), so the
-// 16 lanes of a brick parse up to 16 components side by side; the plane words
-// go to shared memory, and then the brick's lanes rebuild each component's
-// coefficients in ascending order, invert the transform and accumulate.
+// Layout: 4 warps per CTA, two bricks per warp, 16 lanes per brick.  Parsing
+// a component's bit planes is sequential (each plane's length depends on the
+// planes above it), so lanes parse up to 8 components of their brick side by
+// side with a register bit window; the bricks' bit offsets come from one
+// coalesced load of the chunk's 32 brick lengths and a warp scan.  The plane
+// words go to shared memory; then, per component in ascending order, lane p
+// fetches plane p (and p + 32) of both bricks, a 32x32 bit transpose across
+// the warp turns planes back into each lane's coefficients t + 16j, and the
+// inverse reorder, lifting and scaling run through a bank-conflict-free brick
+// buffer before x_j is added into x~.
 #include <type_traits>
 
 #include "pcz_device.cuh"
@@ -24,7 +28,7 @@ __constant__ PermTable kPerm3r = make_perm(64);
 
 constexpr int kRetrieveWarps3 = 4;
 constexpr int kRetrieveThreads3 = 32 * kRetrieveWarps3;
-constexpr int kParseLanes = 16;  // components parsed side by side per brick
+constexpr int kParseLanes = 8;  // components parsed side by side per brick
 
 struct BlockMeta {
   uint64_t off;  // first bit of the brick in the component's payload
@@ -32,12 +36,16 @@ struct BlockMeta {
 };
 
 template <typename T>
-constexpr size_t retrieve_smem3() {
+__host__ __device__ constexpr size_t retrieve_warp_bytes3() {
   using F = Fmt<T>;
-  return (size_t)kRetrieveWarps3 *
-         (2 * kParseLanes * F::P * sizeof(uint64_t)        // plane words
-          + 2 * kParseLanes * sizeof(BlockMeta)            // per-component block header
-          + 2 * 64 * sizeof(typename F::S));               // brick buffer
+  return 2 * kParseLanes * F::P * sizeof(uint64_t)  // plane words
+         + 2 * kParseLanes * sizeof(BlockMeta)      // per-component block header
+         + 128 * sizeof(typename F::S);             // brick buffer of the two bricks
+}
+
+template <typename T>
+constexpr size_t retrieve_smem3() {
+  return (size_t)kRetrieveWarps3 * retrieve_warp_bytes3<T>();
 }
 
 // R11 decoding of planes P-1 .. p of one block, starting at bit pos and ending
@@ -45,19 +53,18 @@ constexpr size_t retrieve_smem3() {
 // where top is the highest non-empty plane (-1 if none).  Returns false on a
 // malformed block; every loop is bounded by N and P.
 template <typename T>
-__device__ bool parse_planes(const uint64_t* __restrict__ w, uint64_t nw, uint64_t pos, uint64_t end, int p,
-                             uint64_t* planes, int& top) {
+__device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, uint64_t* planes, int& top) {
   constexpr int N = 64;
   int n = 0;
   top = -1;
   for (int pl = Fmt<T>::P - 1; pl >= p; --pl) {
     uint64_t W = 0;
     if (n > 0) {
-      W = peek64(w, nw, pos) & low_mask64(n);
+      W = br.peek(pos) & low_mask64(n);
       pos += (uint64_t)n;
     }
-    while (n < N) {
-      const uint64_t v = peek64(w, nw, pos);
+    for (int it = 0; it < N && n < N; ++it) {
+      const uint64_t v = br.peek(pos);
       if (!(v & 1ull)) {  // test 0: nothing more in this plane
         pos += 1;
         break;
@@ -67,7 +74,7 @@ __device__ bool parse_planes(const uint64_t* __restrict__ w, uint64_t nw, uint64
       if (rest) {
         tz = __ffsll((long long)rest) - 1;
       } else {
-        if (!(peek64(w, nw, pos + 64) & 1ull)) return false;
+        if (!(br.peek(pos + 64) & 1ull)) return false;
         tz = 63;
       }
       if (n + tz >= N) return false;  // a promised 1 that never came
@@ -91,16 +98,16 @@ __global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveP
   constexpr int Q = F::P - 2 - Geo<3>::G;
   constexpr int C = Geo<3>::C;
   constexpr int HDR = 2 + 3 + F::EBITS;
+  constexpr bool WIDE = F::P == 64;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int EMAXT = (1 << (F::EXPW - 1));  // frexp exponent of the largest finite T
 
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, t = lane & 15;
-  unsigned char* wbase = smem + (size_t)warp * (2 * kParseLanes * F::P * sizeof(uint64_t) +
-                                                2 * kParseLanes * sizeof(BlockMeta) + 2 * 64 * sizeof(S));
+  unsigned char* wbase = smem + (size_t)warp * retrieve_warp_bytes3<T>();
   uint64_t* planes = reinterpret_cast<uint64_t*>(wbase);
   BlockMeta* meta = reinterpret_cast<BlockMeta*>(planes + 2 * kParseLanes * F::P);
-  S* bbuf = reinterpret_cast<S*>(meta + 2 * kParseLanes) + h * 64;
+  S* buf = reinterpret_cast<S*>(meta + 2 * kParseLanes);
 
   const int64_t g = (int64_t)blockIdx.x * (2 * kRetrieveWarps3) + warp * 2 + h;
   const bool have = g < R.nbox;
@@ -113,6 +120,7 @@ __global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveP
     b = bx + R.nb[0] * (by + R.nb[1] * bz);
   }
   const int64_t chunk = b / kChunk;
+  const int inchunk = (int)(b - chunk * kChunk);
   const int ly = t & 3, lz = t >> 2;
   const int64_t gy = 4 * by + ly, gz = 4 * bz + lz;
   const bool line_ok = have && gy < R.dims[1] && gz < R.dims[2] && gy >= R.lo[1] && gy < R.hi[1] &&
@@ -132,25 +140,62 @@ __global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveP
     xt[m] = T(0);
     if (R.write && R.k0 > 0 && vm[m]) xt[m] = out[orow + 4 * bx + m - R.lo[0]];
   }
-  int pos_r[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) pos_r[j] = kPerm3r.pos[t + 16 * j];
   const int xx = t & 3, yq = t >> 2;
+  int ix[4], iy[4], iz[4], ir[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    ix[m] = sidx<T>(m, ly, lz, h);
+    iy[m] = sidx<T>(xx, m, yq, h);
+    iz[m] = sidx<T>(xx, yq, m, h);
+    const int pos = kPerm3r.pos[t + 16 * m];
+    ir[m] = sidx<T>(pos & 3, (pos >> 2) & 3, pos >> 4, h);
+  }
+  uint32_t tkeep[5];
+  transpose_masks(lane, tkeep);
+  // the two bricks' chunks and places in them, known to every lane
+  const int64_t chunkA = __shfl_sync(FULL, chunk, 0), chunkB = __shfl_sync(FULL, chunk, 16);
+  const int posA = __shfl_sync(FULL, inchunk, 0), posB = __shfl_sync(FULL, inchunk, 16);
+  const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
 
   for (int base = R.k0; base < R.k; base += kParseLanes) {
     const int nc = min(kParseLanes, R.k - base);
+    // bit offsets of both bricks in each component of this round: one coalesced
+    // load of a chunk's 32 brick lengths and a warp scan per (component, brick)
+    uint64_t my_off = 0, my_end = 0;
+    for (int c = 0; c < nc; ++c) {
+      const CompDesc& cd = R.comp[base + c];
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb) {
+        const int64_t ch = hb ? chunkB : chunkA;
+        const bool hv = hb ? haveB : haveA;
+        const int pb = hb ? posB : posA;
+        const int64_t bb = ch * kChunk + lane;
+        const int len = (hv && bb < R.nbricks) ? (int)cd.brick_len[bb] : 0;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int before = __shfl_sync(FULL, incl - len, pb);
+        const int mine = __shfl_sync(FULL, len, pb);
+        if (lane == 16 * hb + c && hv) {
+          my_off = cd.chunk_word[ch] * 64ull + (uint64_t)before;
+          my_end = my_off + (uint64_t)mine;
+        }
+      }
+    }
     if (have && t < nc) {  // lane t parses component base + t of this brick
-      const CompDesc cd = R.comp[base + t];
-      uint64_t off = cd.chunk_word[chunk] * 64ull;
-      for (int64_t bb = chunk * kChunk; bb < b; ++bb) off += cd.brick_len[bb];
-      const uint64_t end = off + cd.brick_len[b];
-      const uint64_t v = peek64(cd.payload, cd.nwords, off);
+      const CompDesc& cd = R.comp[base + t];
+      BitReader br;
+      br.init(cd.payload, cd.nwords, my_off);
+      const uint64_t v = br.peek(my_off);
       int mode = (int)(v & 3ull), s = 0, p = 0, top = -1;
       bool ok;
       if (mode == kModeZero) {
-        ok = end == off + 2;
+        ok = my_end == my_off + 2;
       } else if (mode == kModeRaw) {
-        ok = end == off + 2 + (uint64_t)N * F::P;
+        ok = my_end == my_off + 2 + (uint64_t)N * F::P;
       } else if (mode == kModeCoded) {
         const int esc = (int)((v >> 2) & 7ull);
         const int emax = (int)((v >> 5) & ((1ull << F::EBITS) - 1)) - F::EBIAS;
@@ -158,7 +203,7 @@ __global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveP
         if (ok) {
           s = Q - emax;
           p = min(max(cd.L + s - C - esc, 0), F::P);
-          ok = parse_planes<T>(cd.payload, cd.nwords, off + HDR, end, p, planes + (h * kParseLanes + t) * F::P, top);
+          ok = parse_planes<T>(br, my_off + HDR, my_end, p, planes + (h * kParseLanes + t) * F::P, top);
         }
       } else {
         ok = false;
@@ -168,7 +213,7 @@ __global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveP
         mode = kModeZero;
       }
       BlockMeta bm;
-      bm.off = off;
+      bm.off = my_off;
       bm.mode = mode;
       bm.s = s;
       bm.p = p;
@@ -177,57 +222,74 @@ __global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveP
     }
     __syncwarp();
     for (int jj = 0; jj < nc; ++jj) {  // lines 2-4, components in ascending order
-      BlockMeta my;
-      my.mode = kModeZero;
-      my.s = my.p = 0;
-      my.top = -1;
-      my.off = 0;
-      if (have) my = meta[h * kParseLanes + jj];
+      BlockMeta mA, mB;
+      mA.mode = mB.mode = kModeZero;
+      mA.s = mB.s = mA.p = mB.p = 0;
+      mA.top = mB.top = -1;
+      mA.off = mB.off = 0;
+      if (haveA) mA = meta[jj];
+      if (haveB) mB = meta[kParseLanes + jj];
+      const BlockMeta& my = h ? mB : mA;
       T xi[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) xi[m] = T(0);
-      const bool coded = my.mode == kModeCoded;
-      if (__any_sync(FULL, coded)) {
-        const int hi_ = coded ? my.top : -1;
-        const int lo_ = coded ? my.p : 1 << 20;
-        int phi = max(hi_, __shfl_xor_sync(FULL, hi_, 16));
-        int plo = min(lo_, __shfl_xor_sync(FULL, lo_, 16));
-        U u[4] = {0, 0, 0, 0};
-        const uint64_t* pw = planes + (h * kParseLanes + jj) * F::P;
-        for (int pl = phi; pl >= plo; --pl) {
-          if (coded && pl <= my.top && pl >= my.p) {
-            const uint64_t W = pw[pl];
+      const bool cA = mA.mode == kModeCoded, cB = mB.mode == kModeCoded;
+      if (cA || cB) {
+        // lane l fetches plane l (and l + 32) of both bricks; planes outside
+        // [p, top] are zero
+        const uint64_t* pwA = planes + jj * F::P;
+        const uint64_t* pwB = planes + (kParseLanes + jj) * F::P;
+        const uint64_t WA0 = (cA && lane >= mA.p && lane <= mA.top) ? pwA[lane] : 0ull;
+        const uint64_t WB0 = (cB && lane >= mB.p && lane <= mB.top) ? pwB[lane] : 0ull;
+        U u[4];
+        {
+          uint32_t tl[4];
+          tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
+          tl[1] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x7632);
+          tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
+          tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) u[j] |= (U)((W >> (t + 16 * j)) & 1ull) << pl;
-          }
+          for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep);
+        }
+        if constexpr (WIDE) {
+          const int pl = lane + 32;
+          const uint64_t WA1 = (cA && pl >= mA.p && pl <= mA.top) ? pwA[pl] : 0ull;
+          const uint64_t WB1 = (cB && pl >= mB.p && pl <= mB.top) ? pwB[pl] : 0ull;
+          uint32_t th[4];
+          th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
+          th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
+          th[2] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x5410);
+          th[3] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x7632);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) u[j] |= (U)((uint64_t)transpose32(th[j], lane, tkeep) << 32);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bbuf[pos_r[j]] = nb_inv<T>(u[j]);
+        for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>(u[j]);
         __syncwarp();
         {
-          S a = bbuf[xx + 4 * yq], bq = bbuf[xx + 4 * yq + 16], c = bbuf[xx + 4 * yq + 32], d = bbuf[xx + 4 * yq + 48];
+          S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
           lift_inv(a, bq, c, d);
-          bbuf[xx + 4 * yq] = a; bbuf[xx + 4 * yq + 16] = bq; bbuf[xx + 4 * yq + 32] = c; bbuf[xx + 4 * yq + 48] = d;
+          buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
         }
         __syncwarp();
         {
-          S a = bbuf[xx + 16 * yq], bq = bbuf[xx + 4 + 16 * yq], c = bbuf[xx + 8 + 16 * yq], d = bbuf[xx + 12 + 16 * yq];
+          S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
           lift_inv(a, bq, c, d);
-          bbuf[xx + 16 * yq] = a; bbuf[xx + 4 + 16 * yq] = bq; bbuf[xx + 8 + 16 * yq] = c; bbuf[xx + 12 + 16 * yq] = d;
+          buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
         }
         __syncwarp();
         S r[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) r[m] = bbuf[4 * t + m];
+        for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
         __syncwarp();
         lift_inv(r[0], r[1], r[2], r[3]);
-        if (coded) {
+        if (my.mode == kModeCoded) {
 #pragma unroll
-          for (int m = 0; m < 4; ++m) xi[m] = F::val(dequantize_bits<T>(r[m], my.s));
+          for (int m = 0; m < 4; ++m) xi[m] = dequantize_val<T>(r[m], my.s);
         }
       }
       if (my.mode == kModeRaw) {
-        const CompDesc cd = R.comp[base + jj];
+        const CompDesc& cd = R.comp[base + jj];
 #pragma unroll
         for (int m = 0; m < 4; ++m)
           xi[m] = F::val((U)peek64(cd.payload, cd.nwords, my.off + 2 + (uint64_t)F::P * (4 * t + m)));
