@@ -177,6 +177,7 @@ struct pc_streams {
   uint64_t* d_payload = nullptr;   // all components back to back
   uint64_t* d_chunk_word = nullptr;  // [n][nchunks]
   uint16_t* d_brick_len = nullptr;   // [n][nbricks]
+  uint32_t* d_brick_off = nullptr;   // [n][nbricks] derived: first bit of each brick in its chunk
   CompDesc* d_desc = nullptr;        // [n]
   unsigned int* d_err = nullptr;
 };
@@ -189,6 +190,7 @@ void streams_release(pc_streams* s) {
   cudaFree(s->d_payload);
   cudaFree(s->d_chunk_word);
   cudaFree(s->d_brick_len);
+  cudaFree(s->d_brick_off);
   cudaFree(s->d_desc);
   cudaFree(s->d_err);
   delete s;
@@ -202,6 +204,7 @@ pc_status upload_desc(pc_streams* s, cudaStream_t st) {
     d[i].nwords = s->words[i];
     d[i].chunk_word = s->d_chunk_word + (int64_t)i * s->nchunks;
     d[i].brick_len = s->d_brick_len + (int64_t)i * s->nbricks;
+    d[i].brick_off = s->d_brick_off + (int64_t)i * s->nbricks;
     d[i].L = s->L[i];
     d[i].pad_ = 0;
   }
@@ -245,13 +248,17 @@ pc_status run_retrieve(const pc_streams* s, int k0, int k, const int64_t lo[3], 
   R.out = d_out;
   R.write = write;
   R.err = s->d_err;
-  if (k == k0 && write) {
-    if (k0 == 0) {
+  if (k == k0) {
+    if (k0 == 0 && write) {
       const size_t bytes = (size_t)((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])) * dsize(s->dtype);
       CK(cudaMemsetAsync(d_out, 0, bytes, st));
     }
     return PC_OK;
   }
+  R.umult = retrieve_unit_mult(k - k0);
+  R.grid = retrieve_grid(s->dtype, s->ndims, R.nbox, R.umult);
+  Scratch scr(st);  // per-CTA spill for planes below the shared-memory slots
+  CK(scr.get((void**)&R.spill, 8 * retrieve_spill_words(s->dtype, s->ndims, R.grid)));
   {
     TimedLaunch tl(PC_KERNEL_RETRIEVE, st);
     CK(launch_retrieve(s->dtype, s->ndims, R, st));
@@ -342,6 +349,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
 #undef SCR
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_desc, sizeof(CompDesc) * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 16);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
@@ -349,6 +357,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
       streams_release(s);
       return cuda_fail(e, "allocation");
     }
+    P.brick_off = s->d_brick_off;
     P.chunk_nwords = chunk_nwords;
     P.chunk_pool = chunk_pool;
     P.brick_len = s->d_brick_len;
@@ -654,6 +663,7 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_desc, sizeof(CompDesc) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 16);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
@@ -667,6 +677,7 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
       e = cudaMemcpyAsync(s->d_payload + s->word_base[i], p + off, 8 * s->words[i], cudaMemcpyHostToDevice, st);
     off += 8 * s->words[i];
   }
+  if (e == cudaSuccess) e = launch_brick_offsets(s->d_brick_len, s->d_brick_off, n, nbr, st);
   if (e != cudaSuccess) {
     streams_release(s);
     return cuda_fail(e, "deserialize upload");

@@ -12,9 +12,12 @@
 // and z lifting passes and the reorder go through a bank-conflict-free brick
 // buffer in shared memory.  Bit planes come from 32x32 bit transposes across
 // the warp, after which lane p owns plane p (and p + 32): each lane emits its
-// plane's bits (R11), with the significance count before the plane and the
-// plane's bit offset from suffix scans over lanes (planes are coded from the
-// top down).  The chunk's bits are assembled in shared memory and appended to
+// plane's verbatim bits (R11), with the significance count before the plane
+// and the plane's bit offset from suffix scans over lanes (planes are coded from the
+// top down); the lane holding a coefficient writes the bits of the token that
+// makes it significant, at positions that follow from the plane's offset,
+// its significance count and the coefficient's rank among the plane's new
+// coefficients.  The chunk's bits are assembled in shared memory and appended to
 // a scratch pool with one atomic per chunk; pcz_misc.cu then scans the chunk
 // sizes and packs the final streams.
 #include <climits>
@@ -46,32 +49,26 @@ constexpr size_t compress_smem3() {
   using S = typename Fmt<T>::S;
   return (size_t)chunk_buf_words3<T>() * 4      // chunk bit buffer
          + (size_t)kChunk * 64 * sizeof(S)     // brick buffers, 128 elements per warp
+         + (size_t)kChunk * 64 * 8             // plane words of every brick
+         + (size_t)kChunk * 64 * 4             // plane code offsets and significance counts
          + 32 * 4 * 5                          // lengths, offsets, modes, escalations, violations
          + 16;                                 // pool base
 }
 
-// Writes one plane's code (R11) at bit offset o of buf: n verbatim bits of W,
-// then a test bit 1 and the run up to each newly significant coefficient, and
-// a closing test 0 (a zero bit, already clear) while n < N.
-template <int N>
-__device__ __forceinline__ void write_plane(uint32_t* buf, uint32_t o, uint64_t W, int n) {
-  if (n > 0) or_bits(buf, o, W & low_mask64(n));
-  if (n >= N) return;
-  o += n;
-  uint64_t w = n >= 64 ? 0ull : (W >> n);
-  uint64_t a0 = 0, a1 = 0, a2 = 0;
-  int rel = 0;
-  for (int it = 0; it < 64 && w; ++it) {  // one pass per set bit
-    const int tz = __ffsll((long long)w) - 1;
-    const int r1 = rel, r2 = rel + 1 + tz;  // the test bit and the coefficient's 1
-    if (r1 < 64) a0 |= 1ull << r1; else if (r1 < 128) a1 |= 1ull << (r1 - 64); else a2 |= 1ull << (r1 - 128);
-    if (r2 < 64) a0 |= 1ull << r2; else if (r2 < 128) a1 |= 1ull << (r2 - 64); else a2 |= 1ull << (r2 - 128);
-    rel = r2 + 1;
-    w = tz >= 63 ? 0ull : (w >> (tz + 1));
-  }
-  or_bits(buf, o, a0);
-  or_bits(buf, o + 64, a1);
-  or_bits(buf, o + 128, a2);
+// R11 group-test bits of one coefficient c that turns significant in plane
+// pc (its highest set bit, at or above the lowest coded plane): when n
+// coefficients are significant before pc and c >= n, c is a token of that
+// plane.  With k its rank among the plane's tokens (1-based), the group part
+// of the plane (which follows the n verbatim bits) holds c's 1 at c - n + k,
+// the next token's test bit right after it unless c is the plane's last
+// token, and the plane's first test bit at 0 (set by the token with k = 1).
+// Zeros (runs and the closing test bit) need no write.
+__device__ __forceinline__ void write_token(uint32_t* buf, uint32_t group_base, uint64_t W, int n, int c) {
+  const uint64_t before = W & low_mask64(c) & ~low_mask64(n);
+  const int k = 1 + __popcll((long long)before);
+  const bool last = c >= 63 || (W >> (c + 1)) == 0ull;
+  or_bits(buf, group_base + (uint32_t)(c - n + k), last ? 1ull : 3ull);
+  if (k == 1) atomicOr(buf + (group_base >> 5), 1u << (group_base & 31));
 }
 
 // Suffix scans of one round of 32 planes (lane l = plane base + l, coded in
@@ -121,7 +118,9 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* cbuf = reinterpret_cast<uint32_t*>(smem);
   S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4);
-  int* s_len = reinterpret_cast<int*>(bbuf + kChunk * 64);
+  uint64_t* s_pw = reinterpret_cast<uint64_t*>(bbuf + kChunk * 64);  // [warp][brick][plane] words
+  uint32_t* s_pi = reinterpret_cast<uint32_t*>(s_pw + kChunk * 64);  // [warp][brick][plane] off | n << 16
+  int* s_len = reinterpret_cast<int*>(s_pi + kChunk * 64);
   int* s_off = s_len + 32;
   int* s_mode = s_off + 32;
   int* s_esc = s_mode + 32;
@@ -198,6 +197,8 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
   }
   uint32_t tkeep[5];
   transpose_masks(lane, tkeep);
+  unsigned long long pool_base = 0;  // thread 0 only
+  unsigned pool_nw = 0;
 
   for (int i = 0; i < P.n; ++i) {  // line 2
     const U tb = (U)P.tau_bits[i];
@@ -358,6 +359,20 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
       totB = csum;
     }
     const int lenC = HDR + (h ? totB : totA);
+    {  // plane p's word, code offset and significance count, for the coefficient lanes
+      uint64_t* pw = s_pw + warp * 128;
+      uint32_t* pi = s_pi + warp * 128;
+      pw[lane] = WA0;
+      pi[lane] = (uint32_t)oA0 | ((uint32_t)nA0 << 16);
+      pw[64 + lane] = WB0;
+      pi[64 + lane] = (uint32_t)oB0 | ((uint32_t)nB0 << 16);
+      if constexpr (WIDE) {
+        pw[32 + lane] = WA1;
+        pi[32 + lane] = (uint32_t)oA1 | ((uint32_t)nA1 << 16);
+        pw[96 + lane] = WB1;
+        pi[96 + lane] = (uint32_t)oB1 | ((uint32_t)nB1 << 16);
+      }
+    }
 
     // R14: RAW replaces a longer CODED brick only if it also meets tau_i
     bool raw_ok = false;
@@ -423,15 +438,12 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
         sv += __shfl_xor_sync(FULL, sv, o);
       }
       if (lane == 0) {
-        unsigned long long base = nw ? atomicAdd(P.pool_used, (unsigned long long)nw) : 0ull;
-        if (base + nw > P.pool_words) {
-          atomicOr(P.flags, kFlagPoolOverflow);
-          base = ~0ull;
-        }
-        *s_base = base;
+        // pool space for the chunk; the atomic's result is first needed after
+        // this warp's share of the bit writes, which hides its latency
+        pool_base = nw ? atomicAdd(P.pool_used, (unsigned long long)nw) : 0ull;
+        pool_nw = nw;
         const int64_t ci = (int64_t)i * P.nchunks + chunk;
         P.chunk_nwords[ci] = nw;
-        P.chunk_pool[ci] = base;
         uint32_t* cnt = P.chunk_counts + ci * 5;
         cnt[0] = cz;
         cnt[1] = cc;
@@ -440,9 +452,13 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
         cnt[4] = (uint32_t)sv;
       }
       const int64_t bb = chunk * kChunk + lane;
-      if (bb < P.nbricks) P.brick_len[(int64_t)i * P.nbricks + bb] = (uint16_t)l0;
+      if (bb < P.nbricks) {
+        P.brick_len[(int64_t)i * P.nbricks + bb] = (uint16_t)l0;
+        if (P.brick_off) P.brick_off[(int64_t)i * P.nbricks + bb] = (uint32_t)(incl - l0);
+      }
     }
     __syncthreads();
+    const int chunk_bits = s_off[31] + s_len[31];
 
     // this component's bits of the warp's two bricks, into the chunk buffer
     const uint32_t boff = (uint32_t)s_off[slot];
@@ -455,33 +471,57 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     }
     const int modeA = __shfl_sync(FULL, mode, 0), modeB = __shfl_sync(FULL, mode, 16);
     const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
+    // R11: each coded plane's verbatim bits, by the plane's owner lane ...
     if (haveA && modeA == kModeCoded) {
       const uint32_t base = (uint32_t)s_off[warp * 2] + HDR;
-      if (lane >= pA) write_plane<N>(cbuf, base + oA0, WA0, nA0);
-      if (WIDE && lane + 32 >= pA) write_plane<N>(cbuf, base + oA1, WA1, nA1);
+      if (lane >= pA && nA0 > 0) or_bits(cbuf, base + oA0, WA0 & low_mask64(nA0));
+      if (WIDE && lane + 32 >= pA && nA1 > 0) or_bits(cbuf, base + oA1, WA1 & low_mask64(nA1));
     }
     if (haveB && modeB == kModeCoded) {
       const uint32_t base = (uint32_t)s_off[warp * 2 + 1] + HDR;
-      if (lane >= pB) write_plane<N>(cbuf, base + oB0, WB0, nB0);
-      if (WIDE && lane + 32 >= pB) write_plane<N>(cbuf, base + oB1, WB1, nB1);
+      if (lane >= pB && nB0 > 0) or_bits(cbuf, base + oB0, WB0 & low_mask64(nB0));
+      if (WIDE && lane + 32 >= pB && nB1 > 0) or_bits(cbuf, base + oB1, WB1 & low_mask64(nB1));
+    }
+    // ... and its group-test bits, one token per newly significant coefficient,
+    // by the lane that holds the coefficient
+    if (have && mode == kModeCoded && p < F::P) {
+      const uint64_t* pw = s_pw + warp * 128 + 64 * h;
+      const uint32_t* pi = s_pi + warp * 128 + 64 * h;
+      const uint32_t base = boff + HDR;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if ((u[j] >> p) == 0) continue;  // no bit at or above the lowest coded plane
+        const int pc = F::P - 1 - F::clz(u[j]);
+        const uint32_t info = pi[pc];
+        const int n = (int)(info >> 16), c = t + 16 * j;
+        if (c >= n) write_token(cbuf, base + (info & 0xffffu) + (uint32_t)n, pw[pc], n, c);
+      }
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       xt[m] = xtnew[m];
       e[m] = enew[m];
     }
+    if (tid == 0) {
+      unsigned long long base = pool_base;
+      if (base + pool_nw > P.pool_words) {
+        atomicOr(P.flags, kFlagPoolOverflow);
+        base = ~0ull;
+      }
+      *s_base = base;
+      P.chunk_pool[(int64_t)i * P.nchunks + chunk] = base;
+    }
     __syncthreads();
-    {  // append the chunk to the pool and clear the buffer for the next component
+    {  // append the chunk to the pool and clear the buffer for the next
+       // component (its first writes come after two more barriers)
       const unsigned long long base = *s_base;
-      const int total = s_off[31] + s_len[31];
-      const int nw = (total + 63) >> 6;
+      const int nw = (chunk_bits + 63) >> 6;
       uint64_t* b64 = reinterpret_cast<uint64_t*>(cbuf);
       for (int w = tid; w < nw; w += kCompressThreads3) {
         if (base != ~0ull) P.pool[base + w] = b64[w];
         b64[w] = 0ull;
       }
     }
-    __syncthreads();
   }
 }
 

@@ -26,6 +26,7 @@ struct CompressParams {
   uint32_t* chunk_nwords;        // [n][nchunks] u64 words of each chunk
   uint64_t* chunk_pool;          // [n][nchunks] word offset of each chunk in the pool
   uint16_t* brick_len;           // [n][nbricks] bits of each brick
+  uint32_t* brick_off;           // [n][nbricks] first bit of each brick within its chunk (may be null)
   uint32_t* chunk_counts;        // [n][nchunks][5] ZERO, CODED, RAW, escalations, Eq. 1 failures
   unsigned int* flags;           // bit 0 non-finite input, bit 1 pool too small
 };
@@ -36,6 +37,7 @@ struct CompDesc {
   uint64_t nwords;
   const uint64_t* chunk_word;    // [nchunks] first payload word of each chunk
   const uint16_t* brick_len;     // [nbricks]
+  const uint32_t* brick_off;     // [nbricks] first bit of each brick within its chunk
   int L;                         // floor(log2(tau_i))
   int pad_;
 };
@@ -52,6 +54,9 @@ struct RetrieveParams {
   void* out;                     // box values of T (read too when k0 > 0)
   int write;                     // 0: parse and check only
   unsigned int* err;             // bit 0: a stream failed to parse
+  uint64_t* spill;               // per-CTA plane words that do not fit in shared memory
+  int grid;                      // CTAs launched (persistent over units of bricks)
+  int umult;                     // a unit is 32 * umult bricks (umult > 1 only when k - k0 <= 8)
 };
 
 enum { kFlagNonFinite = 1u, kFlagPoolOverflow = 2u };
@@ -65,6 +70,8 @@ cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint6
 cudaError_t launch_pack(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
                         const uint64_t* word_off, const uint64_t* comp_base, uint64_t* payload, int n,
                         int64_t nchunks, cudaStream_t s);
+cudaError_t launch_brick_offsets(const uint16_t* brick_len, uint32_t* brick_off, int n, int64_t nbricks,
+                                 cudaStream_t s);
 cudaError_t launch_range(int dtype, const void* x, int64_t count, unsigned long long* enc, unsigned int* flags,
                          cudaStream_t s);
 
@@ -75,6 +82,10 @@ void set_last_error(const char* msg);
 int compress_block_threads(int ndims);
 size_t compress_smem_bytes(int dtype, int ndims);
 int retrieve_block_threads(int ndims);
-int retrieve_bricks_per_block(int ndims);
+// CTAs of a persistent retrieval launch over nbox bricks, and the spill words
+// that launch needs (per CTA).
+int retrieve_grid(int dtype, int ndims, int64_t nbox, int umult);
+int retrieve_unit_mult(int ncomp);
+size_t retrieve_spill_words(int dtype, int ndims, int grid);
 
 }  // namespace pcz

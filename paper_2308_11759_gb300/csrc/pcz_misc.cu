@@ -104,6 +104,39 @@ __global__ void __launch_bounds__(256) k_pack(const uint64_t* __restrict__ pool,
   }
 }
 
+// One warp per (component, chunk): each brick's first bit within its chunk,
+// the exclusive prefix sum of the chunk's brick lengths (a derived index the
+// retrieval kernel uses; the stored index holds the lengths).
+__global__ void __launch_bounds__(256) k_brick_offsets(const uint16_t* __restrict__ brick_len,
+                                                       uint32_t* __restrict__ brick_off, int n, int64_t nbricks) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (nbricks + kChunk - 1) / kChunk;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < (int64_t)n * nchunks;
+       wi += warps) {
+    const int64_t comp = wi / nchunks, c = wi % nchunks;
+    const int64_t b = c * kChunk + lane;
+    const uint32_t len = b < nbricks ? brick_len[comp * nbricks + b] : 0u;
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (b < nbricks) brick_off[comp * nbricks + b] = incl - len;
+  }
+}
+
+cudaError_t launch_brick_offsets(const uint16_t* brick_len, uint32_t* brick_off, int n, int64_t nbricks,
+                                 cudaStream_t s) {
+  const int64_t items = (int64_t)n * ((nbricks + kChunk - 1) / kChunk);
+  if (items == 0) return cudaSuccess;
+  int64_t blocks = (items + 7) / 8;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_brick_offsets<<<(unsigned)blocks, 256, 0, s>>>(brick_len, brick_off, n, nbricks);
+  return cudaGetLastError();
+}
+
 // Order-preserving map of a finite T to an unsigned integer.
 template <typename T>
 __device__ __forceinline__ unsigned long long order_key(T v) {

@@ -7,16 +7,19 @@
 // bricks meeting the box are touched: zfp-style blocks decode on their own
 // (Sec. 6.1).
 //
-// Layout: 4 warps per CTA, two bricks per warp, 16 lanes per brick.  Parsing
-// a component's bit planes is sequential (each plane's length depends on the
-// planes above it), so lanes parse up to 8 components of their brick side by
-// side with a register bit window; the bricks' bit offsets come from one
-// coalesced load of the chunk's 32 brick lengths and a warp scan.  The plane
-// words go to shared memory; then, per component in ascending order, lane p
-// fetches plane p (and p + 32) of both bricks, a 32x32 bit transpose across
-// the warp turns planes back into each lane's coefficients t + 16j, and the
-// inverse reorder, lifting and scaling run through a bank-conflict-free brick
-// buffer before x_j is added into x~.
+// Layout: persistent CTAs of 8 warps, each taking units of 32 consecutive
+// bricks of the box.  Components are handled in rounds of up to 8.  Parse
+// phase: warp w decodes the bit planes of component base + w for all 32
+// bricks of the unit, one brick per lane (plane parsing is sequential per
+// block, so this is where the lanes' parallelism comes from); a block's plane
+// words go to a shared-memory slot, counted from its top plane down, and the
+// few planes that do not fit to a per-CTA spill area in global memory.  After
+// a barrier, each warp rebuilds its 4 bricks two at a time (16 lanes per
+// brick, lane t holding the x-line y = t & 3, z = t >> 2): lane p fetches
+// plane p (and p + 32) of both bricks, a 32x32 bit transpose across the warp
+// turns planes back into each lane's coefficients t + 16j, and the inverse
+// reorder, lifting and scaling run through a bank-conflict-free brick buffer;
+// x_j is then added into x~, component by component in ascending order.
 #include <type_traits>
 
 #include "pcz_device.cuh"
@@ -26,9 +29,10 @@ namespace pcz {
 
 __constant__ PermTable kPerm3r = make_perm(64);
 
-constexpr int kRetrieveWarps3 = 4;
-constexpr int kRetrieveThreads3 = 32 * kRetrieveWarps3;
-constexpr int kParseLanes = 8;  // components parsed side by side per brick
+constexpr int kRWarps = 8;
+constexpr int kRThreads = 32 * kRWarps;
+constexpr int kRound = 8;  // components per round: one per warp while parsing
+constexpr int kSlot = 24;  // plane words per block kept in shared memory
 
 struct BlockMeta {
   uint64_t off;  // first bit of the brick in the component's payload
@@ -36,24 +40,29 @@ struct BlockMeta {
 };
 
 template <typename T>
-__host__ __device__ constexpr size_t retrieve_warp_bytes3() {
-  using F = Fmt<T>;
-  return 2 * kParseLanes * F::P * sizeof(uint64_t)  // plane words
-         + 2 * kParseLanes * sizeof(BlockMeta)      // per-component block header
-         + 128 * sizeof(typename F::S);             // brick buffer of the two bricks
+__host__ __device__ constexpr size_t retrieve_smem3() {
+  return (size_t)kRound * 32 * kSlot * sizeof(uint64_t)  // plane slots
+         + (size_t)kRound * 32 * sizeof(BlockMeta)       // block headers
+         + (size_t)kRWarps * 128 * sizeof(typename Fmt<T>::S);  // brick buffers
 }
 
 template <typename T>
-constexpr size_t retrieve_smem3() {
-  return (size_t)kRetrieveWarps3 * retrieve_warp_bytes3<T>();
+__host__ __device__ constexpr int spill_per_block() {  // planes below a block's slot
+  return Fmt<T>::P - kSlot;
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t spill_words_per_cta() {
+  return (size_t)kRound * 32 * spill_per_block<T>();
 }
 
 // R11 decoding of planes P-1 .. p of one block, starting at bit pos and ending
-// exactly at end.  planes[pl] receives plane pl's word for pl in [p, top],
-// where top is the highest non-empty plane (-1 if none).  Returns false on a
-// malformed block; every loop is bounded by N and P.
+// exactly at end.  Plane pl (for pl in [p, top], top = the highest non-empty
+// plane, -1 if none) goes to slot[top - pl], or to spill[top - pl - kSlot]
+// below the slot.  Returns false on a malformed block; every loop is bounded.
 template <typename T>
-__device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, uint64_t* planes, int& top) {
+__device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, uint64_t* slot, uint64_t* spill,
+                             int& top) {
   constexpr int N = 64;
   int n = 0;
   top = -1;
@@ -84,63 +93,200 @@ __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, u
     }
     if (pos > end) return false;
     if (W && top < 0) top = pl;
-    if (top >= 0) planes[pl] = W;
+    if (top >= 0) {
+      const int rel = top - pl;
+      if (rel < kSlot)
+        slot[rel] = W;
+      else
+        spill[rel - kSlot] = W;
+    }
   }
   return pos == end;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveParams R) {
-  using F = Fmt<T>;
-  using U = typename F::U;
-  using S = typename F::S;
-  constexpr int N = 64;
-  constexpr int Q = F::P - 2 - Geo<3>::G;
-  constexpr int C = Geo<3>::C;
-  constexpr int HDR = 2 + 3 + F::EBITS;
-  constexpr bool WIDE = F::P == 64;
-  constexpr unsigned FULL = 0xffffffffu;
-  constexpr int EMAXT = (1 << (F::EXPW - 1));  // frexp exponent of the largest finite T
+// One brick of the unit as seen by this lane: where it is and which of its
+// values this lane's x-line writes.
+struct BrickLane {
+  bool have, line_ok;
+  bool vm[4];
+  int64_t bx, b, orow;
+};
 
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, t = lane & 15;
-  unsigned char* wbase = smem + (size_t)warp * retrieve_warp_bytes3<T>();
-  uint64_t* planes = reinterpret_cast<uint64_t*>(wbase);
-  BlockMeta* meta = reinterpret_cast<BlockMeta*>(planes + 2 * kParseLanes * F::P);
-  S* buf = reinterpret_cast<S*>(meta + 2 * kParseLanes);
-
-  const int64_t g = (int64_t)blockIdx.x * (2 * kRetrieveWarps3) + warp * 2 + h;
-  const bool have = g < R.nbox;
-  int64_t bx = 0, by = 0, bz = 0, b = 0;
-  if (have) {
+__device__ __forceinline__ BrickLane brick_lane(const RetrieveParams& R, int64_t g, int t) {
+  BrickLane L;
+  L.have = g < R.nbox;
+  int64_t bx = 0, by = 0, bz = 0;
+  if (L.have) {
     bx = R.bl[0] + g % R.bn[0];
     const int64_t r = g / R.bn[0];
     by = R.bl[1] + r % R.bn[1];
     bz = R.bl[2] + r / R.bn[1];
-    b = bx + R.nb[0] * (by + R.nb[1] * bz);
   }
-  const int64_t chunk = b / kChunk;
-  const int inchunk = (int)(b - chunk * kChunk);
-  const int ly = t & 3, lz = t >> 2;
-  const int64_t gy = 4 * by + ly, gz = 4 * bz + lz;
-  const bool line_ok = have && gy < R.dims[1] && gz < R.dims[2] && gy >= R.lo[1] && gy < R.hi[1] &&
-                       gz >= R.lo[2] && gz < R.hi[2];
+  L.bx = bx;
+  L.b = bx + R.nb[0] * (by + R.nb[1] * bz);
+  const int64_t gy = 4 * by + (t & 3), gz = 4 * bz + (t >> 2);
+  L.line_ok = L.have && gy < R.dims[1] && gz < R.dims[2] && gy >= R.lo[1] && gy < R.hi[1] && gz >= R.lo[2] &&
+              gz < R.hi[2];
   const int64_t ext0 = R.hi[0] - R.lo[0], ext1 = R.hi[1] - R.lo[1];
-  const int64_t orow = ((gz - R.lo[2]) * ext1 + (gy - R.lo[1])) * ext0;
-  bool vm[4];
+  L.orow = ((gz - R.lo[2]) * ext1 + (gy - R.lo[1])) * ext0 + 4 * bx - R.lo[0];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     const int64_t gx = 4 * bx + m;
-    vm[m] = line_ok && gx < R.dims[0] && gx >= R.lo[0] && gx < R.hi[0];
+    L.vm[m] = L.line_ok && gx < R.dims[0] && gx >= R.lo[0] && gx < R.hi[0];
   }
-  T* out = reinterpret_cast<T*>(R.out);
-  T xt[4];
+  return L;
+}
+
+// Rebuilds one component of the warp's brick pair (lanes 0-15: brick A,
+// 16-31: brick B) from the parsed blocks mA/mB (slots sA/sB, spill pA/pB):
+// returns this lane's 4 values of x_j.
+template <typename T>
+__device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMeta& mB, const uint64_t* sA,
+                                             const uint64_t* sB, const uint64_t* pA, const uint64_t* pB,
+                                             const CompDesc* cd, typename Fmt<T>::S* buf, const int* ix,
+                                             const int* iy, const int* iz, const int* ir, const uint32_t* tkeep,
+                                             int lane, int h, int t, T* xi) {
+  using F = Fmt<T>;
+  using U = typename F::U;
+  using S = typename F::S;
+  constexpr bool WIDE = F::P == 64;
+  const BlockMeta& my = h ? mB : mA;
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {  // line 1, or the partial sum so far
-    xt[m] = T(0);
-    if (R.write && R.k0 > 0 && vm[m]) xt[m] = out[orow + 4 * bx + m - R.lo[0]];
+  for (int m = 0; m < 4; ++m) xi[m] = T(0);
+  const bool cA = mA.mode == kModeCoded, cB = mB.mode == kModeCoded;
+  if (cA || cB) {
+    // lane l fetches plane l (and l + 32) of both bricks; planes outside
+    // [p, top] are zero
+    auto fetch = [&](const BlockMeta& mX, bool cX, const uint64_t* sX, const uint64_t* pX, int pl) {
+      if (!cX || pl < mX.p || pl > mX.top) return (uint64_t)0;
+      const int rel = mX.top - pl;
+      return rel < kSlot ? sX[rel] : pX[rel - kSlot];
+    };
+    const uint64_t WA0 = fetch(mA, cA, sA, pA, lane), WB0 = fetch(mB, cB, sB, pB, lane);
+    U u[4];
+    {
+      uint32_t tl[4];
+      tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
+      tl[1] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x7632);
+      tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
+      tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep);
+    }
+    if constexpr (WIDE) {
+      const uint64_t WA1 = fetch(mA, cA, sA, pA, lane + 32), WB1 = fetch(mB, cB, sB, pB, lane + 32);
+      uint32_t th[4];
+      th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
+      th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
+      th[2] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x5410);
+      th[3] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x7632);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) u[j] |= (U)((uint64_t)transpose32(th[j], lane, tkeep) << 32);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>(u[j]);
+    __syncwarp();
+    {
+      S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
+      lift_inv(a, bq, c, d);
+      buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
+    }
+    __syncwarp();
+    {
+      S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
+      lift_inv(a, bq, c, d);
+      buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
+    }
+    __syncwarp();
+    S r[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
+    __syncwarp();
+    lift_inv(r[0], r[1], r[2], r[3]);
+    if (my.mode == kModeCoded) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) xi[m] = dequantize_val<T>(r[m], my.s);
+    }
   }
-  const int xx = t & 3, yq = t >> 2;
+  if (my.mode == kModeRaw) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      xi[m] = F::val((U)peek64(cd->payload, cd->nwords, my.off + 2 + (uint64_t)F::P * (4 * t + m)));
+  }
+}
+
+// Parse phase: thread L decodes component base + L / ub of unit brick
+// L % ub (ub = bricks per unit) into slot L.
+template <typename T>
+__device__ __forceinline__ void parse_task(const RetrieveParams& R, int64_t unit0, int ub, int base, int nc,
+                                           uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
+  using F = Fmt<T>;
+  constexpr int N = 64;
+  constexpr int Q = F::P - 2 - Geo<3>::G;
+  constexpr int C = Geo<3>::C;
+  constexpr int HDR = 2 + 3 + F::EBITS;
+  constexpr int EMAXT = (1 << (F::EXPW - 1));  // frexp exponent of the largest finite T
+  constexpr int SP = spill_per_block<T>();
+  const int L = threadIdx.x;
+  const int jj = L / ub;
+  const int64_t g = unit0 + L % ub;
+  if (jj >= nc || g >= R.nbox) return;
+  const int64_t bx = R.bl[0] + g % R.bn[0];
+  const int64_t r = g / R.bn[0];
+  const int64_t b = bx + R.nb[0] * ((R.bl[1] + r % R.bn[1]) + R.nb[1] * (R.bl[2] + r / R.bn[1]));
+  const CompDesc& cd = R.comp[base + jj];
+  const uint64_t off = cd.chunk_word[b / kChunk] * 64ull + cd.brick_off[b];
+  const uint64_t end = off + cd.brick_len[b];
+  BitReader br;
+  br.init(cd.payload, cd.nwords, off);
+  const uint64_t v = br.peek(off);
+  int mode = (int)(v & 3ull), s = 0, p = 0, top = -1;
+  bool ok;
+  if (mode == kModeZero) {
+    ok = end == off + 2;
+  } else if (mode == kModeRaw) {
+    ok = end == off + 2 + (uint64_t)N * F::P;
+  } else if (mode == kModeCoded) {
+    const int esc = (int)((v >> 2) & 7ull);
+    const int emax = (int)((v >> 5) & ((1ull << F::EBITS) - 1)) - F::EBIAS;
+    ok = emax >= F::EMIN && emax <= EMAXT;
+    if (ok) {
+      s = Q - emax;
+      p = min(max(cd.L + s - C - esc, 0), F::P);
+      ok = parse_planes<T>(br, off + HDR, end, p, slots + L * kSlot, spill + L * SP, top);
+    }
+  } else {
+    ok = false;
+  }
+  if (!ok) {
+    atomicOr(R.err, 1u);
+    mode = kModeZero;
+  }
+  BlockMeta bm;
+  bm.off = off;
+  bm.mode = mode;
+  bm.s = s;
+  bm.p = p;
+  bm.top = top;
+  meta[L] = bm;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R) {
+  using F = Fmt<T>;
+  using S = typename F::S;
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int SP = spill_per_block<T>();
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* slots = reinterpret_cast<uint64_t*>(smem);                          // [256][kSlot]
+  BlockMeta* meta = reinterpret_cast<BlockMeta*>(slots + kRound * 32 * kSlot);  // [256]
+  S* bufs = reinterpret_cast<S*>(meta + kRound * 32);                           // [kRWarps][128]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, t = lane & 15;
+  S* buf = bufs + warp * 128;
+  uint64_t* spill = R.spill + (size_t)blockIdx.x * spill_words_per_cta<T>();
+
+  const int xx = t & 3, yq = t >> 2, ly = t & 3, lz = t >> 2;
   int ix[4], iy[4], iz[4], ir[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -152,162 +298,142 @@ __global__ void __launch_bounds__(kRetrieveThreads3) k_retrieve3(const RetrieveP
   }
   uint32_t tkeep[5];
   transpose_masks(lane, tkeep);
-  // the two bricks' chunks and places in them, known to every lane
-  const int64_t chunkA = __shfl_sync(FULL, chunk, 0), chunkB = __shfl_sync(FULL, chunk, 16);
-  const int posA = __shfl_sync(FULL, inchunk, 0), posB = __shfl_sync(FULL, inchunk, 16);
-  const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
+  T* out = reinterpret_cast<T*>(R.out);
+  const int ub = 32 * R.umult;  // bricks per unit
+  const int64_t nunits = (R.nbox + ub - 1) / ub;
 
-  for (int base = R.k0; base < R.k; base += kParseLanes) {
-    const int nc = min(kParseLanes, R.k - base);
-    // bit offsets of both bricks in each component of this round: one coalesced
-    // load of a chunk's 32 brick lengths and a warp scan per (component, brick)
-    uint64_t my_off = 0, my_end = 0;
-    for (int c = 0; c < nc; ++c) {
-      const CompDesc& cd = R.comp[base + c];
+  for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    const int64_t unit0 = unit * ub;
+    if (R.k - R.k0 <= kRound) {
+      // one round: every warp parses, then each warp rebuilds its 4 * umult
+      // bricks two at a time and writes them out
+      const int nc = R.k - R.k0;
+      parse_task<T>(R, unit0, ub, R.k0, nc, slots, meta, spill);
+      __syncthreads();
+      for (int q = 0; q < 2 * R.umult; ++q) {
+        const int uA = 4 * R.umult * warp + 2 * q;  // unit-local index of the pair's first brick
+        const BrickLane BL = brick_lane(R, unit0 + uA + h, t);
+        const bool haveA = __shfl_sync(FULL, (int)BL.have, 0) != 0;
+        const bool haveB = __shfl_sync(FULL, (int)BL.have, 16) != 0;
+        T xt[4];
 #pragma unroll
-      for (int hb = 0; hb < 2; ++hb) {
-        const int64_t ch = hb ? chunkB : chunkA;
-        const bool hv = hb ? haveB : haveA;
-        const int pb = hb ? posB : posA;
-        const int64_t bb = ch * kChunk + lane;
-        const int len = (hv && bb < R.nbricks) ? (int)cd.brick_len[bb] : 0;
-        int incl = len;
+        for (int m = 0; m < 4; ++m) {  // line 1, or the partial sum so far
+          xt[m] = T(0);
+          if (R.write && R.k0 > 0 && BL.vm[m]) xt[m] = out[BL.orow + m];
+        }
+        for (int jj = 0; jj < nc; ++jj) {  // lines 2-4, components in ascending order
+          BlockMeta mA, mB;
+          mA.mode = mB.mode = kModeZero;
+          mA.s = mB.s = mA.p = mB.p = 0;
+          mA.top = mB.top = -1;
+          mA.off = mB.off = 0;
+          const int L = jj * ub + uA;
+          if (haveA) mA = meta[L];
+          if (haveB) mB = meta[L + 1];
+          T xi[4];
+          rebuild_pair<T>(mA, mB, slots + L * kSlot, slots + (L + 1) * kSlot, spill + L * SP, spill + (L + 1) * SP,
+                          &R.comp[R.k0 + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(FULL, incl, o);
-          if (lane >= o) incl += y;
+          for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // line 4: x~ += x_j
         }
-        const int before = __shfl_sync(FULL, incl - len, pb);
-        const int mine = __shfl_sync(FULL, len, pb);
-        if (lane == 16 * hb + c && hv) {
-          my_off = cd.chunk_word[ch] * 64ull + (uint64_t)before;
-          my_end = my_off + (uint64_t)mine;
+        if (R.write) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            if (BL.vm[m]) out[BL.orow + m] = xt[m];
         }
+      }
+      __syncthreads();  // the next unit's parse reuses the slots
+    } else {
+      // several rounds (umult = 1): x~ of the warp's 4 bricks stays in
+      // registers across rounds
+      BrickLane BL[2];
+      T xt[2][4];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        BL[q] = brick_lane(R, unit0 + 4 * warp + 2 * q + h, t);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          xt[q][m] = T(0);
+          if (R.write && R.k0 > 0 && BL[q].vm[m]) xt[q][m] = out[BL[q].orow + m];
+        }
+      }
+      for (int base = R.k0; base < R.k; base += kRound) {
+        const int nc = min(kRound, R.k - base);
+        parse_task<T>(R, unit0, 32, base, nc, slots, meta, spill);
+        __syncthreads();
+        for (int jj = 0; jj < nc; ++jj) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int uA = 4 * warp + 2 * q;
+            const bool haveA = __shfl_sync(FULL, (int)BL[q].have, 0) != 0;
+            const bool haveB = __shfl_sync(FULL, (int)BL[q].have, 16) != 0;
+            BlockMeta mA, mB;
+            mA.mode = mB.mode = kModeZero;
+            mA.s = mB.s = mA.p = mB.p = 0;
+            mA.top = mB.top = -1;
+            mA.off = mB.off = 0;
+            const int L = jj * 32 + uA;
+            if (haveA) mA = meta[L];
+            if (haveB) mB = meta[L + 1];
+            T xi[4];
+            rebuild_pair<T>(mA, mB, slots + L * kSlot, slots + (L + 1) * kSlot, spill + L * SP,
+                            spill + (L + 1) * SP, &R.comp[base + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xt[q][m] = F::add(xt[q][m], xi[m]);
+          }
+        }
+        __syncthreads();  // the next round's parse reuses the slots
+      }
+      if (R.write) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            if (BL[q].vm[m]) out[BL[q].orow + m] = xt[q][m];
       }
     }
-    if (have && t < nc) {  // lane t parses component base + t of this brick
-      const CompDesc& cd = R.comp[base + t];
-      BitReader br;
-      br.init(cd.payload, cd.nwords, my_off);
-      const uint64_t v = br.peek(my_off);
-      int mode = (int)(v & 3ull), s = 0, p = 0, top = -1;
-      bool ok;
-      if (mode == kModeZero) {
-        ok = my_end == my_off + 2;
-      } else if (mode == kModeRaw) {
-        ok = my_end == my_off + 2 + (uint64_t)N * F::P;
-      } else if (mode == kModeCoded) {
-        const int esc = (int)((v >> 2) & 7ull);
-        const int emax = (int)((v >> 5) & ((1ull << F::EBITS) - 1)) - F::EBIAS;
-        ok = emax >= F::EMIN && emax <= EMAXT;
-        if (ok) {
-          s = Q - emax;
-          p = min(max(cd.L + s - C - esc, 0), F::P);
-          ok = parse_planes<T>(br, my_off + HDR, my_end, p, planes + (h * kParseLanes + t) * F::P, top);
-        }
-      } else {
-        ok = false;
-      }
-      if (!ok) {
-        atomicOr(R.err, 1u);
-        mode = kModeZero;
-      }
-      BlockMeta bm;
-      bm.off = my_off;
-      bm.mode = mode;
-      bm.s = s;
-      bm.p = p;
-      bm.top = top;
-      meta[h * kParseLanes + t] = bm;
-    }
-    __syncwarp();
-    for (int jj = 0; jj < nc; ++jj) {  // lines 2-4, components in ascending order
-      BlockMeta mA, mB;
-      mA.mode = mB.mode = kModeZero;
-      mA.s = mB.s = mA.p = mB.p = 0;
-      mA.top = mB.top = -1;
-      mA.off = mB.off = 0;
-      if (haveA) mA = meta[jj];
-      if (haveB) mB = meta[kParseLanes + jj];
-      const BlockMeta& my = h ? mB : mA;
-      T xi[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) xi[m] = T(0);
-      const bool cA = mA.mode == kModeCoded, cB = mB.mode == kModeCoded;
-      if (cA || cB) {
-        // lane l fetches plane l (and l + 32) of both bricks; planes outside
-        // [p, top] are zero
-        const uint64_t* pwA = planes + jj * F::P;
-        const uint64_t* pwB = planes + (kParseLanes + jj) * F::P;
-        const uint64_t WA0 = (cA && lane >= mA.p && lane <= mA.top) ? pwA[lane] : 0ull;
-        const uint64_t WB0 = (cB && lane >= mB.p && lane <= mB.top) ? pwB[lane] : 0ull;
-        U u[4];
-        {
-          uint32_t tl[4];
-          tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
-          tl[1] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x7632);
-          tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
-          tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep);
-        }
-        if constexpr (WIDE) {
-          const int pl = lane + 32;
-          const uint64_t WA1 = (cA && pl >= mA.p && pl <= mA.top) ? pwA[pl] : 0ull;
-          const uint64_t WB1 = (cB && pl >= mB.p && pl <= mB.top) ? pwB[pl] : 0ull;
-          uint32_t th[4];
-          th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
-          th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
-          th[2] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x5410);
-          th[3] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x7632);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) u[j] |= (U)((uint64_t)transpose32(th[j], lane, tkeep) << 32);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>(u[j]);
-        __syncwarp();
-        {
-          S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
-          lift_inv(a, bq, c, d);
-          buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
-        }
-        __syncwarp();
-        {
-          S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
-          lift_inv(a, bq, c, d);
-          buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
-        }
-        __syncwarp();
-        S r[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
-        __syncwarp();
-        lift_inv(r[0], r[1], r[2], r[3]);
-        if (my.mode == kModeCoded) {
-#pragma unroll
-          for (int m = 0; m < 4; ++m) xi[m] = dequantize_val<T>(r[m], my.s);
-        }
-      }
-      if (my.mode == kModeRaw) {
-        const CompDesc& cd = R.comp[base + jj];
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-          xi[m] = F::val((U)peek64(cd.payload, cd.nwords, my.off + 2 + (uint64_t)F::P * (4 * t + m)));
-      }
-#pragma unroll
-      for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // line 4: x~ += x_j
-    }
-    __syncwarp();
-  }
-  if (R.write) {
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-      if (vm[m]) out[orow + 4 * bx + m - R.lo[0]] = xt[m];
   }
 }
 
-int retrieve_block_threads(int ndims) { return kRetrieveThreads3; }
-int retrieve_bricks_per_block(int ndims) { return 2 * kRetrieveWarps3; }
+int retrieve_block_threads(int ndims) { return kRThreads; }
+
+// Bricks per unit / 32 so that one round's parse keeps all 8 warps busy.
+int retrieve_unit_mult(int ncomp) {
+  if (ncomp <= 0 || ncomp > kRound) return 1;
+  int u = kRound;
+  while (u > 1 && (u / 2) * ncomp >= kRound) u /= 2;
+  while (u * ncomp > kRound) u /= 2;
+  return u < 1 ? 1 : u;
+}
+
+template <typename T>
+static int retrieve_grid_t(int64_t nbox, int umult) {
+  static int per_sm[2] = {0, 0};  // CTAs per SM that fit (queried once per type)
+  static int sms = 0;
+  int& ps = per_sm[sizeof(T) == 8];
+  if (!ps) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_retrieve3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)retrieve_smem3<T>());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_retrieve3<T>, kRThreads, retrieve_smem3<T>()) !=
+            cudaSuccess ||
+        ps < 1)
+      ps = 1;
+    if (sms < 1) sms = 1;
+  }
+  const int64_t units = (nbox + 32 * umult - 1) / (32 * umult);
+  const int64_t g = (int64_t)ps * sms;
+  return (int)(units < g ? (units > 0 ? units : 1) : g);
+}
+
+int retrieve_grid(int dtype, int ndims, int64_t nbox, int umult) {
+  return dtype == 1 ? retrieve_grid_t<float>(nbox, umult) : retrieve_grid_t<double>(nbox, umult);
+}
+
+size_t retrieve_spill_words(int dtype, int ndims, int grid) {
+  return (dtype == 1 ? spill_words_per_cta<float>() : spill_words_per_cta<double>()) * (size_t)grid;
+}
 
 template <typename T>
 static cudaError_t launch_retrieve_t(const RetrieveParams& p, cudaStream_t s) {
@@ -315,8 +441,7 @@ static cudaError_t launch_retrieve_t(const RetrieveParams& p, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_retrieve3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (p.nbox == 0) return cudaSuccess;
-  const int64_t per = 2 * kRetrieveWarps3;
-  k_retrieve3<T><<<(unsigned)((p.nbox + per - 1) / per), kRetrieveThreads3, smem, s>>>(p);
+  k_retrieve3<T><<<(unsigned)p.grid, kRThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
