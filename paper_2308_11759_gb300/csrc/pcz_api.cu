@@ -286,7 +286,6 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
   for (int a = 0; a < ndims; ++a)
     if (dims[a] < 1) return fail(PC_ERR_ARG, "extent < 1");
   if (!tau_valid(tau, n)) return fail(PC_ERR_TAU_ORDER, "tolerances must be finite, positive, strictly decreasing");
-  if (ndims != 3) return fail(PC_ERR_ARG, "this build codes 3D fields only");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -606,7 +605,9 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   s->dtype = dt;
   s->n = n;
   make_geometry(ndims, dims, s->dims, s->nb, &s->nbricks, &s->nchunks);
-  if (s->nbricks != nbr || s->nchunks != nch || ndims != 3) {
+  bool unit_tail = true;  // extents beyond ndims are 1
+  for (int a = ndims; a < 3; ++a) unit_tail = unit_tail && dims[a] == 1;
+  if (s->nbricks != nbr || s->nchunks != nch || !unit_tail) {
     delete s;
     return fail(PC_ERR_CORRUPT_STREAM, "brick counts do not match the extents");
   }

@@ -542,6 +542,7 @@ static cudaError_t launch_compress_t(const CompressParams& p, cudaStream_t s) {
 }
 
 cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaStream_t s) {
+  if (ndims == 1 || ndims == 2) return launch_compress_small(dtype, ndims, p, s);
   if (ndims != 3) return cudaErrorNotSupported;
   return dtype == 1 ? launch_compress_t<float>(p, s) : launch_compress_t<double>(p, s);
 }

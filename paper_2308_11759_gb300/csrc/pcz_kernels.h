@@ -64,6 +64,9 @@ enum { kFlagNonFinite = 1u, kFlagPoolOverflow = 2u };
 // Launchers (each returns the launch error).
 cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaStream_t s);
 cudaError_t launch_retrieve(int dtype, int ndims, const RetrieveParams& p, cudaStream_t s);
+// 1D and 2D fields (one thread per brick); called by the two above.
+cudaError_t launch_compress_small(int dtype, int ndims, const CompressParams& p, cudaStream_t s);
+cudaError_t launch_retrieve_small(int dtype, int ndims, const RetrieveParams& p, cudaStream_t s);
 cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint64_t* totals,
                                const uint32_t* chunk_counts, unsigned long long* counts, int n,
                                int64_t nchunks, cudaStream_t s);

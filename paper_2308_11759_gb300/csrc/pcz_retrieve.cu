@@ -299,19 +299,19 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
   uint32_t tkeep[5];
   transpose_masks(lane, tkeep);
   T* out = reinterpret_cast<T*>(R.out);
-  const int ub = 32 * R.umult;  // bricks per unit
+  const int ub = 16 * R.umult;  // bricks per unit: umult brick pairs per warp
   const int64_t nunits = (R.nbox + ub - 1) / ub;
 
   for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
     const int64_t unit0 = unit * ub;
     if (R.k - R.k0 <= kRound) {
-      // one round: every warp parses, then each warp rebuilds its 4 * umult
-      // bricks two at a time and writes them out
+      // one round: every warp parses, then each warp rebuilds its umult
+      // brick pairs and writes them out
       const int nc = R.k - R.k0;
       parse_task<T>(R, unit0, ub, R.k0, nc, slots, meta, spill);
       __syncthreads();
-      for (int q = 0; q < 2 * R.umult; ++q) {
-        const int uA = 4 * R.umult * warp + 2 * q;  // unit-local index of the pair's first brick
+      for (int q = 0; q < R.umult; ++q) {
+        const int uA = 2 * (R.umult * warp + q);  // unit-local index of the pair's first brick
         const BrickLane BL = brick_lane(R, unit0 + uA + h, t);
         const bool haveA = __shfl_sync(FULL, (int)BL.have, 0) != 0;
         const bool haveB = __shfl_sync(FULL, (int)BL.have, 16) != 0;
@@ -397,13 +397,13 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
 
 int retrieve_block_threads(int ndims) { return kRThreads; }
 
-// Bricks per unit / 32 so that one round's parse keeps all 8 warps busy.
+// Brick pairs per warp in a unit (a unit is 16 * umult bricks): as many as
+// keep one round's parse tasks (bricks x components) within the CTA's 256
+// threads; several rounds use 2 pairs per warp.
 int retrieve_unit_mult(int ncomp) {
-  if (ncomp <= 0 || ncomp > kRound) return 1;
-  int u = kRound;
-  while (u > 1 && (u / 2) * ncomp >= kRound) u /= 2;
-  while (u * ncomp > kRound) u /= 2;
-  return u < 1 ? 1 : u;
+  if (ncomp <= 0 || ncomp > kRound) return 2;
+  const int m = 16 / ncomp;
+  return m < 1 ? 1 : m;
 }
 
 template <typename T>
@@ -422,16 +422,18 @@ static int retrieve_grid_t(int64_t nbox, int umult) {
       ps = 1;
     if (sms < 1) sms = 1;
   }
-  const int64_t units = (nbox + 32 * umult - 1) / (32 * umult);
+  const int64_t units = (nbox + 16 * umult - 1) / (16 * umult);
   const int64_t g = (int64_t)ps * sms;
   return (int)(units < g ? (units > 0 ? units : 1) : g);
 }
 
 int retrieve_grid(int dtype, int ndims, int64_t nbox, int umult) {
+  if (ndims != 3) return 1;  // the 1D/2D kernel is not persistent
   return dtype == 1 ? retrieve_grid_t<float>(nbox, umult) : retrieve_grid_t<double>(nbox, umult);
 }
 
 size_t retrieve_spill_words(int dtype, int ndims, int grid) {
+  if (ndims != 3) return 0;
   return (dtype == 1 ? spill_words_per_cta<float>() : spill_words_per_cta<double>()) * (size_t)grid;
 }
 
@@ -446,6 +448,7 @@ static cudaError_t launch_retrieve_t(const RetrieveParams& p, cudaStream_t s) {
 }
 
 cudaError_t launch_retrieve(int dtype, int ndims, const RetrieveParams& p, cudaStream_t s) {
+  if (ndims == 1 || ndims == 2) return launch_retrieve_small(dtype, ndims, p, s);
   if (ndims != 3) return cudaErrorNotSupported;
   return dtype == 1 ? launch_retrieve_t<float>(p, s) : launch_retrieve_t<double>(p, s);
 }

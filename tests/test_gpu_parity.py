@@ -33,7 +33,24 @@ CASES = [
     ("thin_3x5x130_f32", lambda: S.powerlaw((3, 5, 130), seed=9, dtype=np.float32), "bin4", 5),
     ("constant", lambda: np.full((9, 8, 7), 1.5), None, 3),
     ("zeros", lambda: np.zeros((8, 8, 8), dtype=np.float32), None, 2),
+    # 2D and 1D fields (4x4 and 4-value bricks)
+    ("pl2d_f32_ragged_decade", lambda: S.powerlaw((157, 389), seed=12, dtype=np.float32), "dec", 8),
+    ("pl2d_f64_bin4", lambda: S.powerlaw((130, 97), seed=13, dtype=np.float64), "bin4", 10),
+    ("gauss2d_f64_decade", lambda: S.gaussians((64, 64), seed=14), "dec", 8),
+    ("steps2d_f32_12", lambda: _steps((75, 66), 15, np.float32), "dec", 12),
+    ("steps2d_f64_12", lambda: _steps((75, 66), 15, np.float64), "dec", 12),
+    ("lossless2d_f32_14", lambda: (10.0 + 4.0 * S.powerlaw((23, 21), seed=22, dtype=np.float32)), "bin4", 14),
+    ("pl1d_f64_decade", lambda: S.powerlaw((4099,), seed=16, dtype=np.float64), "dec", 8),
+    ("pl1d_f32_bin4", lambda: S.powerlaw((1001,), seed=17, dtype=np.float32), "bin4", 6),
+    ("tiny1d_3", lambda: np.array([1.0, 2.0, 7.0]), None, 3),
+    ("thin2d_1x70_f32", lambda: S.powerlaw((1, 70), seed=18, dtype=np.float32), "bin4", 5),
 ]
+
+
+def _steps(shape, seed, dtype):
+    """powerlaw plus jumps of height 3 where it crosses 0.5 (sharp fronts)."""
+    f = S.powerlaw(shape, seed=seed, dtype=np.float64)
+    return (f + np.where(f > 0.5, 3.0, 0.0)).astype(dtype)
 
 
 def _tau(x, kind, n):
