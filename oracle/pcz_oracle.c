@@ -623,16 +623,16 @@ static int code_brick(const field_t *f, const int *perm, int64_t b, const double
   int64_t org[3];
   brick_lanes(f, b, org, inf, src);
   for (int pos = 0; pos < k->N; pos++) x[pos] = load_T(f, lane_index(f, org, src[pos]));
-  for (int pos = 0; pos < k->N; pos++) xt[pos] = 0.0; /* line 1: x~ <- 0 */
-  for (int i = 0; i < n; i++) {                      /* line 2 */
-    for (int pos = 0; pos < k->N; pos++)             /* line 3: e <- x - x~ */
+  for (int pos = 0; pos < k->N; pos++) xt[pos] = 0.0; /* Algorithm 1 starts from x~ = 0 */
+  for (int i = 0; i < n; i++) {                      /* one component per tau_i */
+    for (int pos = 0; pos < k->N; pos++)             /* residual e = x - x~ */
       if (inf[pos]) e[pos] = sub_T(k, x[pos], xt[pos]);
     for (int pos = 0; pos < k->N; pos++)
       if (!inf[pos]) e[pos] = e[src[pos]];
     int64_t start = y[i].n;
-    encode_block(k, perm, e, x, xt, inf, tau[i], &y[i], st[i]); /* line 4: y_i <- C(e, tau_i) */
-    if (decode_block(k, perm, y[i].w, start, y[i].n, tau[i], xi)) return -1; /* line 5: x_i <- D(y_i) */
-    for (int pos = 0; pos < k->N; pos++) /* line 6: x~ <- x~ + x_i */
+    encode_block(k, perm, e, x, xt, inf, tau[i], &y[i], st[i]); /* y_i = C(e, tau_i) */
+    if (decode_block(k, perm, y[i].w, start, y[i].n, tau[i], xi)) return -1; /* x_i = D(y_i) */
+    for (int pos = 0; pos < k->N; pos++) /* x~ = x~ + x_i */
       if (inf[pos]) xt[pos] = add_T(k, xt[pos], xi[pos]);
     for (int pos = 0; pos < k->N; pos++) /* Eq. 1, counted where it fails */
       if (inf[pos] && !(fabs(sub_T(k, x[pos], xt[pos])) <= tau[i])) st[i][ST_VIOL]++;
@@ -811,12 +811,12 @@ int oc_retrieve(const oc_streams *s, int k0, int k, const int64_t *lo_in, const 
     }
     if (!any) continue;
     double xt[OC_MAXN], xi[OC_MAXN];
-    for (int pos = 0; pos < cd->N; pos++) { /* line 1, or the partial sum so far */
+    for (int pos = 0; pos < cd->N; pos++) { /* x~ = 0, or the partial sum so far */
       xt[pos] = 0.0;
       if (k0 > 0 && inbox[pos])
         xt[pos] = cd->dtype == OC_F32 ? (double)((float *)inout)[oidx[pos]] : ((double *)inout)[oidx[pos]];
     }
-    for (int j = k0; j < k; j++) { /* lines 2-4 */
+    for (int j = k0; j < k; j++) { /* Algorithm 2: x~ += D(y_j) */
       int64_t start = brick_bit(s, j, b);
       if (decode_block(cd, perm, s->payload[j], start, start + s->brick_len[j][b], s->tau[j], xi)) {
         bad = 1;
@@ -902,12 +902,12 @@ int oc_decode_brick(int dtype, int d, const double *tau, int k, const uint64_t *
 /* ------------------------------------------------------------------------ */
 void oc_scalar_fl32(const double *x, int64_t count, int n, double *comps) {
   for (int64_t v = 0; v < count; v++) {
-    double xt = 0.0;               /* line 1 */
-    for (int i = 0; i < n; i++) {  /* line 2 */
-      double e = x[v] - xt;        /* line 3 */
-      float y = (float)e;          /* line 4: C = round to float32 */
-      double xi = (double)y;       /* line 5: D = widen back */
-      xt = xt + xi;                /* line 6 */
+    double xt = 0.0;               /* x~ = 0 */
+    for (int i = 0; i < n; i++) {  /* components */
+      double e = x[v] - xt;        /* residual */
+      float y = (float)e;          /* C = round to float32 */
+      double xi = (double)y;       /* D = widen back */
+      xt = xt + xi;                /* partial sum */
       comps[i * count + v] = xi;
     }
   }

@@ -2,9 +2,9 @@
 // Sec. 4.1) for every 4x4x4 brick of a 3D field, all n components in one pass.
 //
 // Per brick and component i the kernel computes the residual e = x - x~_{i-1}
-// (line 3), codes it with the PCZ coder at tau_i (line 4: y_i = C(e, tau_i)),
-// reconstructs x_i = D(y_i) from the coded planes (line 5) and adds it into
-// x~ (line 6).  x and x~ never leave registers, so the field is read once.
+// e = x - x~, codes it with the PCZ coder at tau_i (y_i = C(e, tau_i)),
+// reconstructs x_i = D(y_i) from the coded planes and adds it into
+// x~.  x and x~ never leave registers, so the field is read once.
 //
 // Layout: one CTA per index chunk of 32 bricks (R15), 16 warps; a warp codes
 // two bricks, 16 lanes each; lane t of a brick holds the x-line y = t & 3,
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
       if (line_in && m < nvx && not_finite<T>(x[m])) bad = true;
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(P.flags, kFlagNonFinite);
   }
-  // Algorithm 1, line 1: x~ = 0; the first residual is x - 0
+  // Algorithm 1 starts from x~ = 0; the first residual is x - 0
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     xt[m] = T(0);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
   unsigned long long pool_base = 0;  // thread 0 only
   unsigned pool_nw = 0;
 
-  for (int i = 0; i < P.n; ++i) {  // line 2
+  for (int i = 0; i < P.n; ++i) {  // one component per tau_i
     const U tb = (U)P.tau_bits[i];
     if (any_partial) {  // R4 padding of the residual
       const T last = nvx == 1 ? e[0] : nvx == 2 ? e[1] : nvx == 3 ? e[2] : e[3];
@@ -298,8 +298,8 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
       T xtn[4], en[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const T xi = dequantize_val<T>(r[m], s);  // line 5: x_i = D(y_i)
-        xtn[m] = F::add(xt[m], xi);               // line 6 (candidate)
+        const T xi = dequantize_val<T>(r[m], s);  // x_i = D(y_i)
+        xtn[m] = F::add(xt[m], xi);               // x~ + x_i (candidate)
         en[m] = F::sub(x[m], xtn[m]);             // the next residual
         if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
       }
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     const int mode = zero_blk ? kModeZero : (pass && !(lenC > LEN_RAW && raw_ok)) ? kModeCoded : kModeRaw;
     const int blen = !have ? 0 : mode == kModeZero ? 2 : mode == kModeRaw ? LEN_RAW : lenC;
 
-    // line 6: x~_i and the next residual, committed after the bits are written
+    // x~_i and the next residual, committed after the bits are written
     // (a RAW brick stores the current residual)
     T xtnew[4], enew[4];
     int viol = 0;  // Eq. 1 failures left (only a RAW brick can have them)

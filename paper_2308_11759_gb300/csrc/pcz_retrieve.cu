@@ -317,11 +317,11 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
         const bool haveB = __shfl_sync(FULL, (int)BL.have, 16) != 0;
         T xt[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {  // line 1, or the partial sum so far
+        for (int m = 0; m < 4; ++m) {  // x~ = 0, or the partial sum so far
           xt[m] = T(0);
           if (R.write && R.k0 > 0 && BL.vm[m]) xt[m] = out[BL.orow + m];
         }
-        for (int jj = 0; jj < nc; ++jj) {  // lines 2-4, components in ascending order
+        for (int jj = 0; jj < nc; ++jj) {  // Algorithm 2, components in ascending order
           BlockMeta mA, mB;
           mA.mode = mB.mode = kModeZero;
           mA.s = mB.s = mA.p = mB.p = 0;
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
           rebuild_pair<T>(mA, mB, slots + L * kSlot, slots + (L + 1) * kSlot, spill + L * SP, spill + (L + 1) * SP,
                           &R.comp[R.k0 + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // line 4: x~ += x_j
+          for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // x~ += x_j
         }
         if (R.write) {
 #pragma unroll
