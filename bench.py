@@ -16,6 +16,14 @@ every retrieval is written back to host memory.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pcz|reference]
 
+The line also carries `serving`: the progressive-query workload (16 float32
+256^3 k^-5/3 fields resident on the device, 8 components each; 10,000 seeded
+queries arriving as a Poisson stream at 2,000/s, each a brick-aligned sub-box
+with sides log-uniform in [8, 256] at a relative tolerance log-uniform in
+[1e-7, 1e-1]; 20 GB device-memory budget) replayed through the batched,
+cached server and through the unbatched plain pipeline (one query per
+launch, no cache), with p50/p99 latency from arrival to completion.
+
 With --impl reference the CPU oracle (the test-infrastructure implementation
 of the same method) is timed on a bounded sample of the same workload.  For
 N > 1 (torchrun) every rank runs its own replica: the method has no data-path
@@ -37,6 +45,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_COMP = 8
+METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
+SERVE_WORKLOAD = ("16 device-resident float32 256^3 k^-5/3 fields, 8 components (tau_i = 1e-(i+1) * range); "
+                  "Poisson arrivals at 2000/s; brick-aligned sub-boxes with sides log-uniform in [8, 256]; "
+                  "relative tolerance log-uniform in [1e-7, 1e-1]; 20 GB budget")
 WORKLOAD = ("512^3 random-phase Gaussian field (P(k) ~ k^-5/3, unit variance), float32 and float64, "
             "8 components, tau_i = 1e-(i+1) * range, compress then retrieval at every k = 1..8")
 
@@ -268,6 +280,70 @@ def run_pcz(args, rank, world, device):
                 e2e=e2e, fields=fields)
 
 
+def serve_queries(nq, nfields, size, ranges, seed=41, rate=2000.0):
+    """The seeded request stream: (field, box, tau, k=0) and arrival times."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nq))
+    arrivals -= arrivals[0]
+    qs = []
+    for _ in range(nq):
+        f = int(rng.integers(0, nfields))
+        lo, hi = [], []
+        for _a in range(3):
+            side = 4 * int(round(np.exp(rng.uniform(np.log(8.0), np.log(float(size)))) / 4.0))
+            side = min(max(side, 8), size)
+            o = 4 * int(rng.integers(0, (size - side) // 4 + 1))
+            lo.append(o)
+            hi.append(o + side)
+        rel = 10.0 ** rng.uniform(-7.0, -1.0)
+        qs.append((f, (lo, hi), rel * ranges[f], 0))
+    return qs, arrivals.tolist()
+
+
+def run_serving(args, device):
+    """Replays the request stream through the batched, cached server and
+    through the unbatched plain pipeline; p50/p99 latency and throughput."""
+    import torch
+
+    import paper_2308_11759_gb300 as pcz
+    import synth_fields as S
+
+    size, nf = args.serve_size, 16
+    streams, ranges = [], []
+    for f in range(nf):
+        x = S.powerlaw((size, size, size), seed=100 + f, dtype=np.float32, device=device)
+        lo, hi = pcz.field_range(x)
+        ranges.append(hi - lo)
+        streams.append(pcz.compress(x, pcz.tau_decade(hi - lo, N_COMP)))
+        del x
+    torch.cuda.synchronize()
+    qs, arr = serve_queries(args.serve_queries, nf, size, ranges)
+    budget = 20 * 10 ** 9
+    out = {"workload": SERVE_WORKLOAD, "queries": len(qs), "rate_per_s": 2000, "budget_bytes": budget,
+           "latency": "arrival to the host seeing the batch's completion event; results stay in device memory"}
+    for name, kw in (("batched", {"max_batch": 512}), ("plain", {"serial": True, "cache": False})):
+        srv = pcz.Server(budget, **kw)
+        for st in streams:
+            srv.add_field(st)
+        warm_q, warm_a = serve_queries(64, nf, size, ranges, seed=7)
+        srv.replay(warm_q, [0.0] * len(warm_q))  # warm-up (kernels loaded, arena touched)
+        srv.reset_cache()
+        lat, stats = srv.replay(qs, arr)
+        srv.close()
+        lat_ms = 1e3 * lat
+        out[name] = {"p50_ms": round(float(np.percentile(lat_ms, 50)), 4),
+                     "p99_ms": round(float(np.percentile(lat_ms, 99)), 4),
+                     "mean_ms": round(float(lat_ms.mean()), 4), "max_ms": round(float(lat_ms.max()), 4),
+                     "throughput_qps": round(stats["queries"] / stats["wall_s"], 1),
+                     "gbs_out": round(stats["bytes_out"] / stats["wall_s"] / 1e9, 3),
+                     "batches": stats["batches"], "mean_batch": round(stats["queries"] / max(stats["batches"], 1), 2),
+                     "max_batch": stats["max_batch"], "peak_device_gb": round(stats["peak_device_bytes"] / 1e9, 3),
+                     "wall_s": round(stats["wall_s"], 3)}
+    for st in streams:
+        st.close()
+    return out
+
+
 def oracle_sample(fields_np, sub, nthreads):
     """Times the CPU oracle on a sub^3 corner of each field: Algorithm 1 then
     Algorithm 2 at every k.  Returns (GB/s of raw bytes, seconds, description)."""
@@ -305,6 +381,9 @@ def main():
     ap.add_argument("--dtypes", default="f32,f64", help="field types in a step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-queries", type=int, default=10000)
+    ap.add_argument("--serve-size", type=int, default=256)
     args = ap.parse_args()
     rank, world, local = dist_setup()
     nthreads = os.cpu_count() or 1
@@ -324,7 +403,7 @@ def main():
             vals.append(v)
             secs += s
         value = float(np.mean(vals))
-        line = {"impl": "reference", "metric": "compress/retrieve GB/s vs HBM roofline", "value": round(value, 5),
+        line = {"impl": "reference", "metric": METRIC, "value": round(value, 5),
                 "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(1e3 * secs / args.steps, 3), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
@@ -342,6 +421,11 @@ def main():
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     r = run_pcz(args, rank, world, device)
+    serving = None
+    if not args.no_serving:
+        r["fields"] = {k: v[: args.sample, : args.sample, : args.sample].cpu() for k, v in r["fields"].items()}
+        torch.cuda.empty_cache()
+        serving = run_serving(args, device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -351,7 +435,7 @@ def main():
                "seconds": round(s, 2)}
     if rank == 0:
         line = {
-            "metric": "compress/retrieve GB/s vs HBM roofline",
+            "metric": METRIC,
             "value": round(r["value"], 3),
             "unit": "GB/s",
             "n_gpus": world,
@@ -372,6 +456,7 @@ def main():
             "gpu_launches": r["launches"],
             "kernels": r["kernels"],
             "rates_bits_per_value": {k: v["rates"] for k, v in r["info"].items()},
+            "serving": serving,
         }
         print(json.dumps(line))
     if world > 1:

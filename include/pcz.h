@@ -220,6 +220,82 @@ pc_status pc_compress_noalloc(const void *d_field, const int64_t *dims, int ndim
                               uint64_t *d_chunk_word, uint16_t *d_brick_len, uint64_t *h_words,
                               uint64_t *h_counts, void *cuda_stream);
 
+/*
+ * Progressive-query server.  Serves queries (field, box, tolerance or k)
+ * against component streams resident on the device, the way Sec. 6.1 and 6.2
+ * describe progressive access: the components stay compressed, the blocks a
+ * query needs are decoded on demand and added into x~, and more precision is
+ * more components added to the current approximation.
+ *
+ * Per field the server keeps a cache of partial sums x~ and, per brick, the k
+ * it holds.  A query at k starts a brick from the cache when the cached k is
+ * at most k and decodes only the components above it; other bricks decode
+ * from their first component.  The result is the same either way, bit for
+ * bit: x~_k of pc_retrieve on the same box.  Bricks a query produced in full
+ * at a k above their cached one are written back into the cache.
+ *
+ * Queries are batched continuously: each batch is one launch of the
+ * retrieval kernel over every query admitted for it (all of one dtype), and
+ * the next batch is admitted and launched while the previous one runs.  A
+ * query is admitted when its output box fits in the arena: the part of
+ * hbm_budget_bytes left after the fields' streams, their caches and the
+ * server's own buffers.
+ *
+ * The server reads the pc_streams objects given to it, which must stay alive
+ * and unchanged until pc_server_free.  All work runs on cuda_stream.  Only 3D
+ * fields are served.
+ */
+typedef struct pc_server pc_server; /* opaque */
+
+#define PC_SERVE_NO_CACHE 1 /* decode every query from its first component, keep no cache */
+#define PC_SERVE_SERIAL 2   /* one query per batch and one batch in flight: the unbatched pipeline */
+
+typedef struct {
+  int field;    /* index returned by pc_server_add_field */
+  int k;        /* components to sum, 1..n; 0: the smallest k with tau_k <= tau */
+  double tau;   /* absolute tolerance, used when k == 0 */
+  pc_box box;   /* the box of the field to return (element units, half-open) */
+} pc_query;
+
+typedef struct {
+  double wall_s;               /* from the start of the replay to the last completion */
+  uint64_t batches;            /* retrieval launches */
+  uint64_t queries;            /* queries served */
+  uint64_t bytes_out;          /* result bytes produced */
+  uint64_t max_batch;          /* most queries in one batch */
+  uint64_t peak_device_bytes;  /* fields, caches, buffers and the arena's largest use */
+  uint64_t arena_bytes;        /* size of the result arena */
+} pc_serve_stats;
+
+/* Creates a server.  max_batch (1..65535) bounds the queries of one batch;
+ * flags is a combination of PC_SERVE_*.  PC_ERR_OOM if the budget cannot hold
+ * the server's own buffers. */
+pc_status pc_server_create(uint64_t hbm_budget_bytes, int max_batch, int flags, void *cuda_stream,
+                           pc_server **out);
+
+/* Registers a 3D stream set; *field receives its index.  Allocates its cache
+ * (one value per field element and 5 bytes per brick) unless
+ * PC_SERVE_NO_CACHE.  PC_ERR_OOM if the streams and the cache exceed the
+ * budget.  Fields are added before the first replay. */
+pc_status pc_server_add_field(pc_server *srv, const pc_streams *s, int *field);
+
+/* Runs nq queries as a request stream: query j arrives arrival_s[j] seconds
+ * (non-decreasing) after the call starts, and the call returns when all are
+ * served.  latency_s[j] (host, nq doubles) receives the time from its arrival
+ * to the host seeing its batch complete.  d_out, if not NULL, holds nq device
+ * pointers (NULL entries allowed) that receive a copy of each result box (x
+ * fastest, dtype of the field).  stats may be NULL.  Every query is checked
+ * before any GPU work (PC_ERR_ARG, PC_ERR_TOL_UNREACHABLE, or PC_ERR_OOM for
+ * a box larger than the arena).  Blocks the calling thread. */
+pc_status pc_server_replay(pc_server *srv, const pc_query *queries, const double *arrival_s, int nq,
+                           void *const *d_out, double *latency_s, pc_serve_stats *stats);
+
+/* Forgets every cached partial sum (synchronises cuda_stream). */
+pc_status pc_server_reset_cache(pc_server *srv);
+
+/* Releases the server and its device memory (not the streams).  NULL is a no-op. */
+pc_status pc_server_free(pc_server *srv);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *pc_last_error(void);
 

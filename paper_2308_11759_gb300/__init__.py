@@ -37,6 +37,19 @@ class Box(C.Structure):
     _fields_ = [("lo", C.c_int64 * 3), ("hi", C.c_int64 * 3)]
 
 
+class Query(C.Structure):
+    _fields_ = [("field", C.c_int), ("k", C.c_int), ("tau", C.c_double), ("box", Box)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("batches", C.c_uint64), ("queries", C.c_uint64),
+                ("bytes_out", C.c_uint64), ("max_batch", C.c_uint64), ("peak_device_bytes", C.c_uint64),
+                ("arena_bytes", C.c_uint64)]
+
+
+PC_SERVE_NO_CACHE, PC_SERVE_SERIAL = 1, 2
+
+
 _lib = None
 
 
@@ -63,6 +76,11 @@ def lib():
             "pc_field_range": [vp, C.c_int64, C.c_int, vp, dp, dp],
             "pc_stream_read_index": [vp, C.c_int, u64p, C.POINTER(C.c_uint16), vp],
             "pc_stream_read": [vp, C.c_int, C.c_uint64, C.c_uint64, u64p, vp],
+            "pc_server_create": [C.c_uint64, C.c_int, C.c_int, vp, C.POINTER(vp)],
+            "pc_server_add_field": [vp, vp, ip],
+            "pc_server_replay": [vp, C.POINTER(Query), dp, C.c_int, C.POINTER(vp), dp, C.POINTER(ServeStats)],
+            "pc_server_reset_cache": [vp],
+            "pc_server_free": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -271,6 +289,65 @@ class Streams:
         buf = C.create_string_buffer(n.value)
         _check(lib().pc_streams_serialize(self._h, buf, C.byref(n), _stream_ptr(stream)))
         return buf.raw[: n.value]
+
+
+class Server:
+    """Progressive-query server over device-resident streams (pc_server_*):
+    batched retrieval with a per-field cache of partial sums, admission by a
+    device-memory budget."""
+
+    def __init__(self, budget_bytes: int, max_batch: int = 256, cache: bool = True, serial: bool = False,
+                 stream=None):
+        flags = (0 if cache else PC_SERVE_NO_CACHE) | (PC_SERVE_SERIAL if serial else 0)
+        self._h = C.c_void_p()
+        self._fields = []  # keeps the Streams objects alive
+        _check(lib().pc_server_create(int(budget_bytes), int(max_batch), flags, _stream_ptr(stream),
+                                      C.byref(self._h)))
+
+    def add_field(self, streams: "Streams") -> int:
+        fid = C.c_int()
+        _check(lib().pc_server_add_field(self._h, streams._h, C.byref(fid)))
+        self._fields.append(streams)
+        return fid.value
+
+    def replay(self, queries, arrival_s, outs=None):
+        """queries: list of (field, box, tau, k) with box = (lo, hi) in array
+        axis order (k = 0: take k from tau); arrival_s: non-decreasing
+        seconds.  outs: optional list of CUDA tensors (or None) receiving the
+        results.  Returns (latencies in seconds as a numpy array, stats dict)."""
+        nq = len(queries)
+        qa = (Query * max(nq, 1))()
+        for j, (field, box, tau, k) in enumerate(queries):
+            known = 0 <= field < len(self._fields)  # the library rejects other indices
+            shape = self._fields[field].shape if known else tuple(box[1])
+            b, _ = _box(box, shape)
+            qa[j].field = int(field)
+            qa[j].k = int(k)
+            qa[j].tau = float(tau)
+            qa[j].box = b if b is not None else _box(([0] * len(shape), list(shape)), shape)[0]
+        arr = (C.c_double * max(nq, 1))(*[float(t) for t in arrival_s])
+        lat = (C.c_double * max(nq, 1))()
+        outp = None
+        if outs is not None:
+            outp = (C.c_void_p * max(nq, 1))(*[(o.data_ptr() if o is not None else None) for o in outs])
+        st = ServeStats()
+        _check(lib().pc_server_replay(self._h, qa, arr, nq, outp, lat, C.byref(st)))
+        stats = {name: getattr(st, name) for name, _ in ServeStats._fields_}
+        return np.frombuffer(lat, dtype=np.float64, count=nq).copy(), stats
+
+    def reset_cache(self):
+        _check(lib().pc_server_reset_cache(self._h))
+
+    def close(self):
+        if self._h:
+            lib().pc_server_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def compress(x, tau, stream=None) -> Streams:

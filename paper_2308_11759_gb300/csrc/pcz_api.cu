@@ -15,7 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pcz.h"
-#include "pcz_kernels.h"
+#include "pcz_host.h"
 
 using namespace pcz;
 
@@ -161,27 +161,6 @@ struct TimedLaunch {
 
 void pcz::set_last_error(const char* msg) { g_err = msg; }
 
-struct pc_streams {
-  int device = 0;
-  int ndims = 0;
-  int64_t dims[3] = {1, 1, 1};
-  int64_t nb[3] = {1, 1, 1};
-  int64_t nbricks = 0, nchunks = 0;
-  pc_dtype dtype = PC_F32;
-  int n = 0;
-  double tau[kMaxComponents] = {};
-  int L[kMaxComponents] = {};
-  uint64_t words[kMaxComponents] = {};      // payload words per component
-  uint64_t word_base[kMaxComponents] = {};  // component's first word in d_payload
-  uint64_t counts[kMaxComponents][5] = {};
-  uint64_t* d_payload = nullptr;   // all components back to back
-  uint64_t* d_chunk_word = nullptr;  // [n][nchunks]
-  uint16_t* d_brick_len = nullptr;   // [n][nbricks]
-  uint32_t* d_brick_off = nullptr;   // [n][nbricks] derived: first bit of each brick in its chunk
-  CompDesc* d_desc = nullptr;        // [n]
-  unsigned int* d_err = nullptr;
-};
-
 namespace {
 
 void streams_release(pc_streams* s) {
@@ -226,28 +205,32 @@ pc_status box_of(const pc_streams* s, const pc_box* box, int64_t lo[3], int64_t 
   return PC_OK;
 }
 
+// One retrieval job over the box of a stream set (units not yet placed).
+BoxJob make_job(const pc_streams* s, int k0, int k, const int64_t lo[3], const int64_t hi[3], void* d_out) {
+  BoxJob J;
+  std::memset(&J, 0, sizeof(J));
+  J.comp = s->d_desc;
+  for (int a = 0; a < 3; ++a) {
+    J.dims[a] = s->dims[a];
+    J.nb[a] = s->nb[a];
+    J.lo[a] = lo[a];
+    J.hi[a] = hi[a];
+    J.bl[a] = lo[a] / 4;
+    J.bn[a] = (hi[a] - 1) / 4 - J.bl[a] + 1;
+  }
+  J.nbox = J.bn[0] * J.bn[1] * J.bn[2];
+  J.k0 = k0;
+  J.k = k;
+  J.umult = retrieve_unit_mult(k - k0);
+  J.out = d_out;
+  return J;
+}
+
+int64_t job_units(const BoxJob& J) { return (J.nbox + 16 * J.umult - 1) / (16 * J.umult); }
+
 // Runs Algorithm 2 on the box: components k0+1..k added into d_out (device).
 pc_status run_retrieve(const pc_streams* s, int k0, int k, const int64_t lo[3], const int64_t hi[3], void* d_out,
                        int write, cudaStream_t st) {
-  RetrieveParams R;
-  std::memset(&R, 0, sizeof(R));
-  R.comp = s->d_desc;
-  for (int a = 0; a < 3; ++a) {
-    R.dims[a] = s->dims[a];
-    R.nb[a] = s->nb[a];
-    R.lo[a] = lo[a];
-    R.hi[a] = hi[a];
-    R.bl[a] = lo[a] / 4;
-    R.bn[a] = (hi[a] - 1) / 4 - R.bl[a] + 1;
-  }
-  R.nbricks = s->nbricks;
-  R.nchunks = s->nchunks;
-  R.k0 = k0;
-  R.k = k;
-  R.nbox = R.bn[0] * R.bn[1] * R.bn[2];
-  R.out = d_out;
-  R.write = write;
-  R.err = s->d_err;
   if (k == k0) {
     if (k0 == 0 && write) {
       const size_t bytes = (size_t)((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])) * dsize(s->dtype);
@@ -255,8 +238,15 @@ pc_status run_retrieve(const pc_streams* s, int k0, int k, const int64_t lo[3], 
     }
     return PC_OK;
   }
-  R.umult = retrieve_unit_mult(k - k0);
-  R.grid = retrieve_grid(s->dtype, s->ndims, R.nbox, R.umult);
+  RetrieveParams R;
+  std::memset(&R, 0, sizeof(R));
+  R.job0 = make_job(s, k0, k, lo, hi, d_out);
+  R.jobs = nullptr;
+  R.njobs = 1;
+  R.nunits = job_units(R.job0);
+  R.write = write;
+  R.err = s->d_err;
+  R.grid = retrieve_grid(s->dtype, s->ndims, R.nunits);
   Scratch scr(st);  // per-CTA spill for planes below the shared-memory slots
   CK(scr.get((void**)&R.spill, 8 * retrieve_spill_words(s->dtype, s->ndims, R.grid)));
   {
@@ -267,6 +257,17 @@ pc_status run_retrieve(const pc_streams* s, int k0, int k, const int64_t lo[3], 
 }
 
 }  // namespace
+
+pc_status pcz::api_fail(pc_status st, const std::string& msg) { return fail(st, msg); }
+pc_status pcz::api_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+size_t pcz::dtype_size(pc_dtype t) { return dsize(t); }
+pc_status pcz::check_box(const pc_streams* s, const pc_box* box, int64_t lo[3], int64_t hi[3]) {
+  return box_of(s, box, lo, hi);
+}
+BoxJob pcz::make_box_job(const pc_streams* s, int k0, int k, const int64_t lo[3], const int64_t hi[3], void* out) {
+  return make_job(s, k0, k, lo, hi, out);
+}
+int64_t pcz::box_job_units(const BoxJob& J) { return job_units(J); }
 
 extern "C" {
 

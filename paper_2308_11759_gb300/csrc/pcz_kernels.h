@@ -42,21 +42,35 @@ struct CompDesc {
   int pad_;
 };
 
-// Launch parameters of the retrieval kernel (Algorithm 2 on the bricks that
-// meet a box, components k0+1..k).
-struct RetrieveParams {
-  const CompDesc* comp;          // device array of n descriptors
-  int64_t dims[3], nb[3], nbricks, nchunks;
-  int k0, k;
+// One box of one field for the retrieval kernel (Algorithm 2 on the bricks
+// that meet the box, components k0+1..k).  A launch runs a list of jobs, each
+// on its own units of bricks.
+struct BoxJob {
+  const CompDesc* comp;          // device array of the field's n descriptors
+  int64_t dims[3], nb[3];
   int64_t lo[3], hi[3];          // box, element units, half-open
   int64_t bl[3], bn[3];          // first brick and brick counts of the box
   int64_t nbox;                  // bricks meeting the box
+  int64_t unit_begin;            // first unit of this job within the launch
+  int k0, k;
+  int umult;                     // a unit is 16 * umult bricks
+  int pad_;
   void* out;                     // box values of T (read too when k0 > 0)
+  const void* cache;             // full-field cached partial sums of T, or null
+  const uint8_t* level;          // per brick: k of the cached partial sum (0: none)
+};
+
+// Launch parameters of the retrieval kernel.
+struct RetrieveParams {
+  BoxJob job0;                   // the job when jobs is null
+  const BoxJob* jobs;            // device array of njobs jobs sorted by unit_begin, or null
+  int njobs;
   int write;                     // 0: parse and check only
+  int64_t nunits;                // units over all jobs
   unsigned int* err;             // bit 0: a stream failed to parse
   uint64_t* spill;               // per-CTA plane words that do not fit in shared memory
-  int grid;                      // CTAs launched (persistent over units of bricks)
-  int umult;                     // a unit is 32 * umult bricks (umult > 1 only when k - k0 <= 8)
+  int grid;                      // CTAs launched (persistent over units)
+  int pad_;
 };
 
 enum { kFlagNonFinite = 1u, kFlagPoolOverflow = 2u };
@@ -87,7 +101,7 @@ size_t compress_smem_bytes(int dtype, int ndims);
 int retrieve_block_threads(int ndims);
 // CTAs of a persistent retrieval launch over nbox bricks, and the spill words
 // that launch needs (per CTA).
-int retrieve_grid(int dtype, int ndims, int64_t nbox, int umult);
+int retrieve_grid(int dtype, int ndims, int64_t nunits);
 int retrieve_unit_mult(int ncomp);
 size_t retrieve_spill_words(int dtype, int ndims, int grid);
 

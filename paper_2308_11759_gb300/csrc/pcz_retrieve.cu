@@ -7,8 +7,15 @@
 // bricks meeting the box are touched: zfp-style blocks decode on their own
 // (Sec. 6.1).
 //
-// Layout: persistent CTAs of 8 warps, each taking units of 32 consecutive
-// bricks of the box.  Components are handled in rounds of up to 8.  Parse
+// A launch runs a list of box jobs (one box of one field each; a single
+// retrieval is a list of one, a batch of queries a longer one), each cut into
+// units of consecutive bricks of its box.  A job may carry a cache of partial
+// sums with, per brick, the k it holds: a brick whose cached k is at most the
+// job's k starts from the cached x~ and decodes only the components above it
+// (Algorithm 2's partial sums are the same whichever way they are reached).
+//
+// Layout: persistent CTAs of 8 warps, each taking units of 16 * umult
+// consecutive bricks of a job's box.  Components are handled in rounds of up to 8.  Parse
 // phase: warp w decodes the bit planes of component base + w for all 32
 // bricks of the unit, one brick per lane (plane parsing is sequential per
 // block, so this is where the lanes' parallelism comes from); a block's plane
@@ -109,32 +116,58 @@ __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, u
 struct BrickLane {
   bool have, line_ok;
   bool vm[4];
-  int64_t bx, b, orow;
+  int64_t bx, b, orow, frow;
 };
 
-__device__ __forceinline__ BrickLane brick_lane(const RetrieveParams& R, int64_t g, int t) {
+__device__ __forceinline__ BrickLane brick_lane(const BoxJob& J, int64_t g, int t) {
   BrickLane L;
-  L.have = g < R.nbox;
+  L.have = g < J.nbox;
   int64_t bx = 0, by = 0, bz = 0;
   if (L.have) {
-    bx = R.bl[0] + g % R.bn[0];
-    const int64_t r = g / R.bn[0];
-    by = R.bl[1] + r % R.bn[1];
-    bz = R.bl[2] + r / R.bn[1];
+    bx = J.bl[0] + g % J.bn[0];
+    const int64_t r = g / J.bn[0];
+    by = J.bl[1] + r % J.bn[1];
+    bz = J.bl[2] + r / J.bn[1];
   }
   L.bx = bx;
-  L.b = bx + R.nb[0] * (by + R.nb[1] * bz);
+  L.b = bx + J.nb[0] * (by + J.nb[1] * bz);
   const int64_t gy = 4 * by + (t & 3), gz = 4 * bz + (t >> 2);
-  L.line_ok = L.have && gy < R.dims[1] && gz < R.dims[2] && gy >= R.lo[1] && gy < R.hi[1] && gz >= R.lo[2] &&
-              gz < R.hi[2];
-  const int64_t ext0 = R.hi[0] - R.lo[0], ext1 = R.hi[1] - R.lo[1];
-  L.orow = ((gz - R.lo[2]) * ext1 + (gy - R.lo[1])) * ext0 + 4 * bx - R.lo[0];
+  L.line_ok = L.have && gy < J.dims[1] && gz < J.dims[2] && gy >= J.lo[1] && gy < J.hi[1] && gz >= J.lo[2] &&
+              gz < J.hi[2];
+  const int64_t ext0 = J.hi[0] - J.lo[0], ext1 = J.hi[1] - J.lo[1];
+  L.orow = ((gz - J.lo[2]) * ext1 + (gy - J.lo[1])) * ext0 + 4 * bx - J.lo[0];
+  L.frow = (gz * J.dims[1] + gy) * J.dims[0] + 4 * bx;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     const int64_t gx = 4 * bx + m;
-    L.vm[m] = L.line_ok && gx < R.dims[0] && gx >= R.lo[0] && gx < R.hi[0];
+    L.vm[m] = L.line_ok && gx < J.dims[0] && gx >= J.lo[0] && gx < J.hi[0];
   }
   return L;
+}
+
+// Level of brick b's cached partial sum that a job at k may start from (0:
+// none): components up to it are already summed in the cache.
+__device__ __forceinline__ int cached_level(const BoxJob& J, int64_t b) {
+  if (!J.level) return 0;
+  const int lv = J.level[b];
+  return lv <= J.k ? lv : 0;
+}
+
+// x~ of this lane's 4 values at the start of a job: 0, the caller's partial
+// sum x~_k0 (refinement), or the cache.
+template <typename T>
+__device__ __forceinline__ void start_sum(const BoxJob& J, int write, const BrickLane& BL, T* xt) {
+  const int lv = BL.have ? cached_level(J, BL.b) : 0;
+  const T* cache = reinterpret_cast<const T*>(J.cache);
+  const T* out = reinterpret_cast<const T*>(J.out);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    xt[m] = T(0);
+    if (lv > 0 && BL.vm[m])
+      xt[m] = cache[BL.frow + m];
+    else if (write && J.k0 > 0 && BL.vm[m])
+      xt[m] = out[BL.orow + m];
+  }
 }
 
 // Rebuilds one component of the warp's brick pair (lanes 0-15: brick A,
@@ -216,10 +249,11 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
 }
 
 // Parse phase: thread L decodes component base + L / ub of unit brick
-// L % ub (ub = bricks per unit) into slot L.
+// L % ub (ub = bricks per unit) into slot L.  Components a brick takes from
+// the cache are not parsed (ZERO).
 template <typename T>
-__device__ __forceinline__ void parse_task(const RetrieveParams& R, int64_t unit0, int ub, int base, int nc,
-                                           uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
+__device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, int64_t unit0, int ub, int base,
+                                           int nc, uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
   using F = Fmt<T>;
   constexpr int N = 64;
   constexpr int Q = F::P - 2 - Geo<3>::G;
@@ -230,11 +264,20 @@ __device__ __forceinline__ void parse_task(const RetrieveParams& R, int64_t unit
   const int L = threadIdx.x;
   const int jj = L / ub;
   const int64_t g = unit0 + L % ub;
-  if (jj >= nc || g >= R.nbox) return;
-  const int64_t bx = R.bl[0] + g % R.bn[0];
-  const int64_t r = g / R.bn[0];
-  const int64_t b = bx + R.nb[0] * ((R.bl[1] + r % R.bn[1]) + R.nb[1] * (R.bl[2] + r / R.bn[1]));
-  const CompDesc& cd = R.comp[base + jj];
+  if (jj >= nc || g >= J.nbox) return;
+  const int64_t bx = J.bl[0] + g % J.bn[0];
+  const int64_t r = g / J.bn[0];
+  const int64_t b = bx + J.nb[0] * ((J.bl[1] + r % J.bn[1]) + J.nb[1] * (J.bl[2] + r / J.bn[1]));
+  if (base + jj < cached_level(J, b)) {
+    BlockMeta bm;
+    bm.off = 0;
+    bm.mode = kModeZero;
+    bm.s = bm.p = 0;
+    bm.top = -1;
+    meta[L] = bm;
+    return;
+  }
+  const CompDesc& cd = J.comp[base + jj];
   const uint64_t off = cd.chunk_word[b / kChunk] * 64ull + cd.brick_off[b];
   const uint64_t end = off + cd.brick_len[b];
   BitReader br;
@@ -259,7 +302,7 @@ __device__ __forceinline__ void parse_task(const RetrieveParams& R, int64_t unit
     ok = false;
   }
   if (!ok) {
-    atomicOr(R.err, 1u);
+    atomicOr(err, 1u);
     mode = kModeZero;
   }
   BlockMeta bm;
@@ -298,29 +341,44 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
   }
   uint32_t tkeep[5];
   transpose_masks(lane, tkeep);
-  T* out = reinterpret_cast<T*>(R.out);
-  const int ub = 16 * R.umult;  // bricks per unit: umult brick pairs per warp
-  const int64_t nunits = (R.nbox + ub - 1) / ub;
+  __shared__ BoxJob sJ;
+  const BoxJob& J = sJ;
+  constexpr int JW = (int)(sizeof(BoxJob) / 8);
+  static_assert(sizeof(BoxJob) % 8 == 0 && JW <= kRThreads, "job copy");
 
-  for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
-    const int64_t unit0 = unit * ub;
-    if (R.k - R.k0 <= kRound) {
+  for (int64_t unit = blockIdx.x; unit < R.nunits; unit += gridDim.x) {
+    __syncthreads();  // the previous unit is done with sJ
+    if (!R.jobs) {
+      if (threadIdx.x == 0) sJ = R.job0;
+    } else if (threadIdx.x < JW) {  // the job whose units contain this one
+      int lo = 0, hi = R.njobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (R.jobs[mid].unit_begin <= unit)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      reinterpret_cast<uint64_t*>(&sJ)[threadIdx.x] = reinterpret_cast<const uint64_t*>(R.jobs + lo)[threadIdx.x];
+    }
+    __syncthreads();
+    T* out = reinterpret_cast<T*>(J.out);
+    const int umult = J.umult;
+    const int ub = 16 * umult;  // bricks per unit: umult brick pairs per warp
+    const int64_t unit0 = (unit - J.unit_begin) * ub;
+    if (J.k - J.k0 <= kRound) {
       // one round: every warp parses, then each warp rebuilds its umult
       // brick pairs and writes them out
-      const int nc = R.k - R.k0;
-      parse_task<T>(R, unit0, ub, R.k0, nc, slots, meta, spill);
+      const int nc = J.k - J.k0;
+      parse_task<T>(J, R.err, unit0, ub, J.k0, nc, slots, meta, spill);
       __syncthreads();
-      for (int q = 0; q < R.umult; ++q) {
-        const int uA = 2 * (R.umult * warp + q);  // unit-local index of the pair's first brick
-        const BrickLane BL = brick_lane(R, unit0 + uA + h, t);
+      for (int q = 0; q < umult; ++q) {
+        const int uA = 2 * (umult * warp + q);  // unit-local index of the pair's first brick
+        const BrickLane BL = brick_lane(J, unit0 + uA + h, t);
         const bool haveA = __shfl_sync(FULL, (int)BL.have, 0) != 0;
         const bool haveB = __shfl_sync(FULL, (int)BL.have, 16) != 0;
         T xt[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {  // x~ = 0, or the partial sum so far
-          xt[m] = T(0);
-          if (R.write && R.k0 > 0 && BL.vm[m]) xt[m] = out[BL.orow + m];
-        }
+        start_sum<T>(J, R.write, BL, xt);
         for (int jj = 0; jj < nc; ++jj) {  // Algorithm 2, components in ascending order
           BlockMeta mA, mB;
           mA.mode = mB.mode = kModeZero;
@@ -332,7 +390,7 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
           if (haveB) mB = meta[L + 1];
           T xi[4];
           rebuild_pair<T>(mA, mB, slots + L * kSlot, slots + (L + 1) * kSlot, spill + L * SP, spill + (L + 1) * SP,
-                          &R.comp[R.k0 + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
+                          &J.comp[J.k0 + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
           for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // x~ += x_j
         }
@@ -342,24 +400,19 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
             if (BL.vm[m]) out[BL.orow + m] = xt[m];
         }
       }
-      __syncthreads();  // the next unit's parse reuses the slots
     } else {
-      // several rounds (umult = 1): x~ of the warp's 4 bricks stays in
-      // registers across rounds
+      // several rounds (umult = 2, units of 32 bricks): x~ of the warp's 4
+      // bricks stays in registers across rounds
       BrickLane BL[2];
       T xt[2][4];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        BL[q] = brick_lane(R, unit0 + 4 * warp + 2 * q + h, t);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          xt[q][m] = T(0);
-          if (R.write && R.k0 > 0 && BL[q].vm[m]) xt[q][m] = out[BL[q].orow + m];
-        }
+        BL[q] = brick_lane(J, unit0 + 4 * warp + 2 * q + h, t);
+        start_sum<T>(J, R.write, BL[q], xt[q]);
       }
-      for (int base = R.k0; base < R.k; base += kRound) {
-        const int nc = min(kRound, R.k - base);
-        parse_task<T>(R, unit0, 32, base, nc, slots, meta, spill);
+      for (int base = J.k0; base < J.k; base += kRound) {
+        const int nc = min(kRound, J.k - base);
+        parse_task<T>(J, R.err, unit0, 32, base, nc, slots, meta, spill);
         __syncthreads();
         for (int jj = 0; jj < nc; ++jj) {
 #pragma unroll
@@ -377,7 +430,7 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
             if (haveB) mB = meta[L + 1];
             T xi[4];
             rebuild_pair<T>(mA, mB, slots + L * kSlot, slots + (L + 1) * kSlot, spill + L * SP,
-                            spill + (L + 1) * SP, &R.comp[base + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
+                            spill + (L + 1) * SP, &J.comp[base + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
             for (int m = 0; m < 4; ++m) xt[q][m] = F::add(xt[q][m], xi[m]);
           }
@@ -407,7 +460,7 @@ int retrieve_unit_mult(int ncomp) {
 }
 
 template <typename T>
-static int retrieve_grid_t(int64_t nbox, int umult) {
+static int retrieve_grid_t(int64_t nunits) {
   static int per_sm[2] = {0, 0};  // CTAs per SM that fit (queried once per type)
   static int sms = 0;
   int& ps = per_sm[sizeof(T) == 8];
@@ -422,14 +475,13 @@ static int retrieve_grid_t(int64_t nbox, int umult) {
       ps = 1;
     if (sms < 1) sms = 1;
   }
-  const int64_t units = (nbox + 16 * umult - 1) / (16 * umult);
   const int64_t g = (int64_t)ps * sms;
-  return (int)(units < g ? (units > 0 ? units : 1) : g);
+  return (int)(nunits < g ? (nunits > 0 ? nunits : 1) : g);
 }
 
-int retrieve_grid(int dtype, int ndims, int64_t nbox, int umult) {
+int retrieve_grid(int dtype, int ndims, int64_t nunits) {
   if (ndims != 3) return 1;  // the 1D/2D kernel is not persistent
-  return dtype == 1 ? retrieve_grid_t<float>(nbox, umult) : retrieve_grid_t<double>(nbox, umult);
+  return dtype == 1 ? retrieve_grid_t<float>(nunits) : retrieve_grid_t<double>(nunits);
 }
 
 size_t retrieve_spill_words(int dtype, int ndims, int grid) {
@@ -442,7 +494,7 @@ static cudaError_t launch_retrieve_t(const RetrieveParams& p, cudaStream_t s) {
   const size_t smem = retrieve_smem3<T>();
   cudaError_t e = cudaFuncSetAttribute(k_retrieve3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (p.nbox == 0) return cudaSuccess;
+  if (p.nunits == 0) return cudaSuccess;
   k_retrieve3<T><<<(unsigned)p.grid, kRThreads, smem, s>>>(p);
   return cudaGetLastError();
 }

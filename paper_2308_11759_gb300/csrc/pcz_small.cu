@@ -327,26 +327,27 @@ __global__ void __launch_bounds__(kSmallThreads) k_retrieve_small(const Retrieve
   constexpr int C = Geo<D>::C;
   constexpr int HDR = 2 + 3 + F::EBITS;
   constexpr int EMAXT = (1 << (F::EXPW - 1));
+  const BoxJob& J = R.job0;  // one job per launch
 
   const int64_t g = (int64_t)blockIdx.x * kSmallThreads + threadIdx.x;
-  if (g >= R.nbox) return;  // no warp-collective operations below
-  const int64_t bx = R.bl[0] + g % R.bn[0];
-  const int64_t by = D == 2 ? R.bl[1] + g / R.bn[0] : 0;
-  const int64_t b = bx + R.nb[0] * by;
-  const int64_t ext0 = R.hi[0] - R.lo[0];
-  T* out = reinterpret_cast<T*>(R.out);
+  if (g >= J.nbox) return;  // no warp-collective operations below
+  const int64_t bx = J.bl[0] + g % J.bn[0];
+  const int64_t by = D == 2 ? J.bl[1] + g / J.bn[0] : 0;
+  const int64_t b = bx + J.nb[0] * by;
+  const int64_t ext0 = J.hi[0] - J.lo[0];
+  T* out = reinterpret_cast<T*>(J.out);
   bool vm[N];
   int64_t oi[N];
   T xt[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const int64_t gx = 4 * bx + (k & 3), gy = 4 * by + (k >> 2);
-    vm[k] = gx < R.dims[0] && gx >= R.lo[0] && gx < R.hi[0] && gy < R.dims[1] && gy >= R.lo[1] && gy < R.hi[1];
-    oi[k] = (gy - R.lo[1]) * ext0 + (gx - R.lo[0]);
-    xt[k] = (R.write && R.k0 > 0 && vm[k]) ? out[oi[k]] : T(0);  // 0, or the partial sum so far
+    vm[k] = gx < J.dims[0] && gx >= J.lo[0] && gx < J.hi[0] && gy < J.dims[1] && gy >= J.lo[1] && gy < J.hi[1];
+    oi[k] = (gy - J.lo[1]) * ext0 + (gx - J.lo[0]);
+    xt[k] = (R.write && J.k0 > 0 && vm[k]) ? out[oi[k]] : T(0);  // 0, or the partial sum so far
   }
-  for (int j = R.k0; j < R.k; ++j) {  // Algorithm 2: x~ += D(y_j)
-    const CompDesc& cd = R.comp[j];
+  for (int j = J.k0; j < J.k; ++j) {  // Algorithm 2: x~ += D(y_j)
+    const CompDesc& cd = J.comp[j];
     const uint64_t off = cd.chunk_word[b / kChunk] * 64ull + cd.brick_off[b];
     const uint64_t end = off + cd.brick_len[b];
     BitReader br;
@@ -454,8 +455,9 @@ cudaError_t launch_compress_small(int dtype, int ndims, const CompressParams& p,
 
 template <typename T, int D>
 static cudaError_t launch_retrieve_small_t(const RetrieveParams& p, cudaStream_t s) {
-  if (p.nbox == 0) return cudaSuccess;
-  k_retrieve_small<T, D><<<(unsigned)((p.nbox + kSmallThreads - 1) / kSmallThreads), kSmallThreads, 0, s>>>(p);
+  if (p.jobs || p.njobs != 1) return cudaErrorNotSupported;
+  if (p.job0.nbox == 0) return cudaSuccess;
+  k_retrieve_small<T, D><<<(unsigned)((p.job0.nbox + kSmallThreads - 1) / kSmallThreads), kSmallThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
