@@ -41,6 +41,7 @@ def lib():
             "oc_chunk_word": (u64p, [vp, C.c_int]),
             "oc_brick_len": (C.POINTER(C.c_uint16), [vp, C.c_int]),
             "oc_stats": (None, [vp, C.c_int, i64p]),
+            "oc_measured": (C.c_double, [vp, C.c_int]),
             "oc_final_xt": (None, [vp, vp]),
             "oc_retrieve": (C.c_int, [vp, C.c_int, C.c_int, i64p, i64p, vp]),
             "oc_free": (None, [vp]),
@@ -131,6 +132,11 @@ class Streams:
     def brick_len(self, i: int) -> np.ndarray:
         L = lib()
         return np.ctypeslib.as_array(L.oc_brick_len(self._h, i), shape=(self.nbricks,)).copy()
+
+    def measured(self, i: int) -> float:
+        """Computed tolerance of component i+1 (Sec. 4.3): max over the field of
+        |fl_T(x - x~_{i+1})|."""
+        return float(lib().oc_measured(self._h, i))
 
     def stats(self, i: int) -> np.ndarray:
         out = np.zeros(5, dtype=np.int64)

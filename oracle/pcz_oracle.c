@@ -20,7 +20,8 @@
  *   - Algorithm 2: x~ <- 0; for i = 1..m: x~ <- x~ + D(y_i); continuing the loop
  *     later refines an existing x~ (Sec. 4.2).
  *   - Eq. 1: ||x - x~_i||_inf <= tau_i, which may fail by O(eps) in floating
- *     point (Sec. 4.3).
+ *     point (Sec. 4.3).  The computed tolerance of component i (Sec. 4.3:
+ *     tau_i <- ||x - x~_i||_inf, kept as metadata) is recorded too.
  *   - zfp-style coding of single d-dimensional blocks of 4^d values with one
  *     exponent per block and component (Sec. 4.4, Sec. 6.1) and group-tested
  *     bit planes (Sec. 2).
@@ -616,7 +617,7 @@ static int decode_block(const coder *k, const int *perm, const uint64_t *w, int6
  * sum x~_n (in-field lanes); st[i] the per-component counters.
  * Returns 0, or -1 if D(y_i) ever failed to read back C's output. */
 static int code_brick(const field_t *f, const int *perm, int64_t b, const double *tau, int n, bits_t *y,
-                      double *xt, int64_t (*st)[ST_N]) {
+                      double *xt, int64_t (*st)[ST_N], double *maxerr) {
   const coder *k = &f->cd;
   double x[OC_MAXN], e[OC_MAXN], xi[OC_MAXN];
   int inf[OC_MAXN], src[OC_MAXN];
@@ -634,8 +635,12 @@ static int code_brick(const field_t *f, const int *perm, int64_t b, const double
     if (decode_block(k, perm, y[i].w, start, y[i].n, tau[i], xi)) return -1; /* x_i = D(y_i) */
     for (int pos = 0; pos < k->N; pos++) /* x~ = x~ + x_i */
       if (inf[pos]) xt[pos] = add_T(k, xt[pos], xi[pos]);
-    for (int pos = 0; pos < k->N; pos++) /* Eq. 1, counted where it fails */
-      if (inf[pos] && !(fabs(sub_T(k, x[pos], xt[pos])) <= tau[i])) st[i][ST_VIOL]++;
+    for (int pos = 0; pos < k->N; pos++) { /* Eq. 1, counted where it fails */
+      if (!inf[pos]) continue;
+      double r = fabs(sub_T(k, x[pos], xt[pos]));
+      if (!(r <= tau[i])) st[i][ST_VIOL]++;
+      if (maxerr && r > maxerr[i]) maxerr[i] = r; /* Sec. 4.3: the computed tolerance */
+    }
   }
   return 0;
 }
@@ -655,6 +660,7 @@ struct oc_streams {
   uint64_t *chunk_word[OC_MAXC];
   uint16_t *brick_len[OC_MAXC];
   int64_t stats[OC_MAXC][ST_N];
+  double measured[OC_MAXC]; /* max over the field of |fl_T(x - x~_i)| (Sec. 4.3) */
   double *xt; /* x~_n of every field value, as produced by Algorithm 1 */
   int status; /* 0 ok, -1 a block failed to decode, -2 a brick exceeded 65535 bits */
 };
@@ -700,6 +706,7 @@ oc_streams *oc_compress(const void *data, int dtype, int ndims, const int64_t *d
   /* chunk_bits[c * n + i]: the bits of component i+1 for the bricks of chunk c */
   bits_t *chunk_bits = (bits_t *)calloc((size_t)(s->nchunks * n), sizeof(bits_t));
   int64_t(*cst)[OC_MAXC][ST_N] = calloc((size_t)s->nchunks, sizeof(*cst));
+  double(*cme)[OC_MAXC] = calloc((size_t)s->nchunks, sizeof(*cme));
   int bad = 0;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -710,7 +717,7 @@ oc_streams *oc_compress(const void *data, int dtype, int ndims, const int64_t *d
     bits_t one[OC_MAXC];
     for (int64_t b = c * OC_CHUNK; b < nb && b < (c + 1) * OC_CHUNK; b++) {
       memset(one, 0, sizeof(bits_t) * (size_t)n);
-      if (code_brick(&s->f, perm, b, tau, n, one, xt, cst[c])) bad |= 1;
+      if (code_brick(&s->f, perm, b, tau, n, one, xt, cst[c], cme[c])) bad |= 1;
       for (int i = 0; i < n; i++) {
         if (one[i].n > 65535) bad |= 2;
         s->brick_len[i][b] = (uint16_t)one[i].n;
@@ -728,7 +735,11 @@ oc_streams *oc_compress(const void *data, int dtype, int ndims, const int64_t *d
   for (int64_t c = 0; c < s->nchunks; c++)
     for (int i = 0; i < n; i++)
       for (int t = 0; t < ST_N; t++) s->stats[i][t] += cst[c][i][t];
+  for (int64_t c = 0; c < s->nchunks; c++)
+    for (int i = 0; i < n; i++)
+      if (cme[c][i] > s->measured[i]) s->measured[i] = cme[c][i];
   free(cst);
+  free(cme);
   for (int i = 0; i < n; i++) {
     int64_t words = 0;
     for (int64_t c = 0; c < s->nchunks; c++) {
@@ -755,6 +766,7 @@ int64_t oc_payload_words(const oc_streams *s, int i) { return s->nwords[i]; }
 const uint64_t *oc_payload(const oc_streams *s, int i) { return s->payload[i]; }
 const uint64_t *oc_chunk_word(const oc_streams *s, int i) { return s->chunk_word[i]; }
 const uint16_t *oc_brick_len(const oc_streams *s, int i) { return s->brick_len[i]; }
+double oc_measured(const oc_streams *s, int i) { return s->measured[i]; }
 void oc_stats(const oc_streams *s, int i, int64_t *out) {
   for (int t = 0; t < ST_N; t++) out[t] = s->stats[i][t];
 }
@@ -865,7 +877,7 @@ int oc_code_brick(const void *data, int dtype, int ndims, const int64_t *dims, c
   bits_t y[OC_MAXC];
   memset(y, 0, sizeof(y));
   int64_t(*stv)[ST_N] = calloc((size_t)n, sizeof(*stv));
-  int rc = code_brick(&f, perm, b, tau, n, y, xt, stv);
+  int rc = code_brick(&f, perm, b, tau, n, y, xt, stv, NULL);
   for (int i = 0; i < n; i++) {
     nbits[i] = y[i].n;
     if ((y[i].n + 63) / 64 > maxwords) rc = rc ? rc : -2;

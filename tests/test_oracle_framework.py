@@ -54,6 +54,27 @@ def test_eq1_bound_and_monotone_error(coded):
         assert s.stats(k - 1)[O.ST_VIOL] == 0
 
 
+def test_measured_error_is_computed_tolerance(coded):
+    """Sec. 4.3: the computed tolerance of component i is ||x - x~_i||_inf,
+    here evaluated independently by numpy on Algorithm 2's reconstruction; it
+    never exceeds the prescribed tau_i, and the query on computed tolerances
+    never needs more components than the query on prescribed ones."""
+    x, tau, s = coded
+    meas = [s.measured(i) for i in range(s.n)]
+    for k in range(1, s.n + 1):
+        assert meas[k - 1] == _err_T(x, s.retrieve(k)), k
+        assert meas[k - 1] <= tau[k - 1]
+    rng = np.random.default_rng(2)
+    for t in tau[0] * 10.0 ** (-rng.uniform(0.0, 9.0, 20)):
+        if t < min(meas):
+            continue
+        km = min(i + 1 for i in range(s.n) if meas[i] <= t)
+        assert km == O.query_k(meas, t)
+        assert _err_T(x, s.retrieve(km)) <= t
+        if t >= tau[-1]:
+            assert km <= O.query_k(tau, t)
+
+
 def test_alg2_reproduces_alg1_sum(coded):
     x, tau, s = coded
     assert np.array_equal(s.retrieve(s.n), s.final_xt())
@@ -122,6 +143,12 @@ def test_lossless_limit(dtype, n):
     assert tau[-1] < ulp
     s = O.Streams(x, tau)
     assert np.array_equal(s.retrieve(n).view(np.uint8), x.view(np.uint8))
+    # the computed tolerance reaches 0 exactly where x~ first equals x
+    meas = [s.measured(i) for i in range(n)]
+    k0 = next(i + 1 for i in range(n) if meas[i] == 0.0)
+    assert np.array_equal(s.retrieve(k0).view(np.uint8), x.view(np.uint8))
+    assert not np.array_equal(s.retrieve(k0 - 1), x)
+    assert all(m == 0.0 for m in meas[k0 - 1:])
 
 
 def test_zero_field_is_all_zero_blocks():
