@@ -187,7 +187,8 @@ def run_pcz(args, rank, world, device):
         cb, rb, pay = algorithmic_bytes(st, fb)
         info[name] = dict(field_bytes=fb, compress_bytes=cb, retrieve_bytes=rb,
                           rates=[round(8 * p / nvox, 4) for p in pay],
-                          counts=[st.counts(i) for i in range(st.n)])
+                          counts=[st.counts(i) for i in range(st.n)],
+                          measured_over_tau=[float("%.4g" % (st.measured_error(i) / st.tau(i))) for i in range(st.n)])
 
     bus = None
     try:
@@ -329,8 +330,16 @@ def run_serving(args, device):
         srv.replay(warm_q, [0.0] * len(warm_q))  # warm-up (kernels loaded, arena touched)
         srv.reset_cache()
         lat, stats = srv.replay(qs, arr)
+        srv.reset_cache()
+        blat, bstats = srv.replay(qs, [0.0] * len(qs))  # saturation: the whole stream waiting at once
         srv.close()
         lat_ms = 1e3 * lat
+        burst = {"throughput_qps": round(bstats["queries"] / bstats["wall_s"], 1),
+                 "gbs_out": round(bstats["bytes_out"] / bstats["wall_s"] / 1e9, 3),
+                 "p50_ms": round(float(np.percentile(1e3 * blat, 50)), 3),
+                 "p99_ms": round(float(np.percentile(1e3 * blat, 99)), 3),
+                 "mean_batch": round(bstats["queries"] / max(bstats["batches"], 1), 2),
+                 "wall_s": round(bstats["wall_s"], 3)}
         out[name] = {"p50_ms": round(float(np.percentile(lat_ms, 50)), 4),
                      "p99_ms": round(float(np.percentile(lat_ms, 99)), 4),
                      "mean_ms": round(float(lat_ms.mean()), 4), "max_ms": round(float(lat_ms.max()), 4),
@@ -338,9 +347,35 @@ def run_serving(args, device):
                      "gbs_out": round(stats["bytes_out"] / stats["wall_s"] / 1e9, 3),
                      "batches": stats["batches"], "mean_batch": round(stats["queries"] / max(stats["batches"], 1), 2),
                      "max_batch": stats["max_batch"], "peak_device_gb": round(stats["peak_device_bytes"] / 1e9, 3),
-                     "wall_s": round(stats["wall_s"], 3)}
+                     "wall_s": round(stats["wall_s"], 3), "all_at_once": burst}
     for st in streams:
         st.close()
+    return out
+
+
+def run_lossless(device):
+    """Sec. 5.1.3 on synthetic fields: components (binary schedule, delta = 4,
+    8 and 16) until the computed tolerance is 0, the bits per value that takes
+    (index included), and the lossless compression ratio."""
+    import torch
+
+    import paper_2308_11759_gb300 as pcz
+    import synth_fields as S
+
+    out = {}
+    cases = (("powerlaw_128^3_f32", lambda: S.powerlaw((128,) * 3, seed=2, dtype=np.float32, device=device)),
+             ("powerlaw_128^3_f64", lambda: S.powerlaw((128,) * 3, seed=2, dtype=np.float64, device=device)),
+             ("fronts_128^3_f64", lambda: S.fronts((128,) * 3, seed=5, dtype=np.float64, device=device)),
+             ("gaussians_64^3_f64", lambda: torch.from_numpy(S.gaussians((64,) * 3, seed=1)).to(device)))
+    for name, make in cases:
+        x = make().contiguous()
+        out[name] = {}
+        for delta in (4, 8, 16):
+            r = pcz.lossless_sweep(x, delta=delta)
+            out[name][f"delta{delta}"] = {"components": r["k"],
+                                          "bits_per_value": round(r["bits_per_value"], 3) if r["k"] else None,
+                                          "ratio": round(r["ratio"], 3) if r["k"] else None}
+            r["streams"].close()
     return out
 
 
@@ -382,6 +417,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-lossless", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=10000)
     ap.add_argument("--serve-size", type=int, default=256)
     args = ap.parse_args()
@@ -426,6 +462,7 @@ def main():
         r["fields"] = {k: v[: args.sample, : args.sample, : args.sample].cpu() for k, v in r["fields"].items()}
         torch.cuda.empty_cache()
         serving = run_serving(args, device)
+    lossless = None if args.no_lossless else run_lossless(device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -456,6 +493,8 @@ def main():
             "gpu_launches": r["launches"],
             "kernels": r["kernels"],
             "rates_bits_per_value": {k: v["rates"] for k, v in r["info"].items()},
+            "computed_tolerances": {k: v["measured_over_tau"] for k, v in r["info"].items()},
+            "lossless": lossless,
             "serving": serving,
         }
         print(json.dumps(line))

@@ -83,6 +83,19 @@ pc_status pc_compress(const void *field, const int64_t *dims, int ndims, pc_dtyp
 pc_status pc_query_k(const pc_streams *s, double tau, int *k_out);
 
 /*
+ * Computed tolerances (Sec. 4.3: tau_i <- ||x - x~_i||_inf kept as metadata, a
+ * tighter bound than the prescribed tau_i).  pc_compress records, per
+ * component, the largest |fl_T(x - x~_i)| over the field (evaluated in the
+ * field's type; 0 once x~_i reproduces x, the lossless limit of Sec. 5.1.3).
+ * pc_stream_measured_error returns it for component i (0-based, double,
+ * exact).  pc_query_k_measured is pc_query_k on these values: the smallest k
+ * with measured_k <= tau, never more components than pc_query_k needs;
+ * PC_ERR_TOL_UNREACHABLE when tau is below every measured error.
+ */
+pc_status pc_stream_measured_error(const pc_streams *s, int i, double *err);
+pc_status pc_query_k_measured(const pc_streams *s, double tau, int *k_out);
+
+/*
  * Algorithm 2 (Sec. 4.2): x~_k = fl(...fl(fl(0 + D(y_1)) + D(y_2))... + D(y_k)),
  * written for the box into out (device or host pointer to the box's values,
  * x fastest, dtype of the field).  If tau >= 0, k is taken from pc_query_k(tau)

@@ -65,6 +65,8 @@ def lib():
         sig = {
             "pc_compress": [vp, i64p, C.c_int, C.c_int, dp, C.c_int, vp, C.POINTER(vp)],
             "pc_query_k": [vp, C.c_double, ip],
+            "pc_query_k_measured": [vp, C.c_double, ip],
+            "pc_stream_measured_error": [vp, C.c_int, dp],
             "pc_retrieve": [vp, C.c_double, C.c_int, C.POINTER(Box), vp, vp],
             "pc_refine": [vp, C.c_int, C.c_int, C.POINTER(Box), vp, vp],
             "pc_stream_info": [vp, C.c_int, dp, u64p, u64p],
@@ -206,10 +208,19 @@ class Streams:
             pass
 
     # ---- queries --------------------------------------------------------
-    def query_k(self, tau: float) -> int:
+    def query_k(self, tau: float, measured: bool = False) -> int:
+        """Components a query at tolerance tau needs: on the prescribed
+        tolerances (Sec. 6.2), or on the computed ones (Sec. 4.3)."""
         k = C.c_int()
-        _check(lib().pc_query_k(self._h, float(tau), C.byref(k)))
+        fn = lib().pc_query_k_measured if measured else lib().pc_query_k
+        _check(fn(self._h, float(tau), C.byref(k)))
         return k.value
+
+    def measured_error(self, i: int) -> float:
+        """Computed tolerance of component i+1: max |fl(x - x~_{i+1})| (Sec. 4.3)."""
+        e = C.c_double()
+        _check(lib().pc_stream_measured_error(self._h, i, C.byref(e)))
+        return e.value
 
     def tau(self, i: int) -> float:
         t = C.c_double()
@@ -378,6 +389,29 @@ def tau_decade(rng: float, n: int, first_exp: int = 2):
     """tau_i = 10^-(first_exp + i - 1) * tau_0 for i = 1..n: each decimal factor
     is the double nearest to it, times the range with one rounding."""
     return [float("1e-%d" % (first_exp + i - 1)) * rng for i in range(1, n + 1)]
+
+
+def lossless_sweep(x, delta: int = 4, n_max: int = 64, stream=None):
+    """Sec. 5.1.3: components are added until x~ reproduces x.  Compresses x
+    with the binary schedule tau_i = 2^(-delta i) * range, i = 1..n_max, and
+    returns dict(k = the first component whose computed tolerance is 0 (None
+    if none), bits_per_value = stream bits of components 1..k including their
+    index, ratio = bits of the type / bits_per_value, measured = the computed
+    tolerances).  The streams object is returned under "streams"."""
+    rng = value_range(x, stream)
+    if rng == 0.0:
+        rng = max(abs(field_range(x, stream)[0]), 1.0)
+    tau = [t for t in tau_binary(rng, delta, n_max) if t > 0.0]
+    st = compress(x, tau, stream)
+    meas = [st.measured_error(i) for i in range(st.n)]
+    k = next((i + 1 for i, m in enumerate(meas) if m == 0.0), None)
+    nvals = int(np.prod(st.shape))
+    bits = None
+    if k is not None:
+        bits = sum(st.info(i)[1] + 8 * st.info(i)[2] for i in range(k)) / nvals
+    tbits = 32 if st.dtype in (_torch().float32,) else 64
+    return {"k": k, "bits_per_value": bits, "ratio": (tbits / bits) if bits else None, "measured": meas,
+            "streams": st}
 
 
 KERNEL_KINDS = ("compress", "scan", "pack", "retrieve", "range")

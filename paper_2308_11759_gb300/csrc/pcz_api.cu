@@ -41,7 +41,8 @@ pc_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr uint32_t kMagic = 0x315a4350u;  // "PCZ1"
-constexpr uint32_t kFormatVersion = 1;
+constexpr uint32_t kFormatVersion = 2;
+constexpr size_t kCompRecord = 64;  // serialized bytes per component record
 
 size_t dsize(pc_dtype t) { return t == PC_F32 ? 4 : 8; }
 
@@ -105,6 +106,19 @@ uint64_t tau_threshold_bits(double tau, pc_dtype dt) {
   uint32_t b;
   std::memcpy(&b, &f, 4);
   return b;
+}
+
+// The T value of a bit pattern, as a double (exact).
+double value_of_bits(uint64_t b, pc_dtype dt) {
+  if (dt == PC_F64) {
+    double d;
+    std::memcpy(&d, &b, 8);
+    return d;
+  }
+  const uint32_t u = (uint32_t)b;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
 }
 
 bool tau_valid(const double* tau, int n) {
@@ -338,7 +352,11 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
     unsigned int* flags = nullptr;
     unsigned long long* used = nullptr;
     uint64_t* comp_base = nullptr;
+    uint64_t* chunk_maxerr = nullptr;
+    unsigned long long* maxerr = nullptr;
     SCR(chunk_nwords, 4 * n * nch);
+    SCR(chunk_maxerr, 8 * n * nch);
+    SCR(maxerr, 8 * n);
     SCR(chunk_pool, 8 * n * nch);
     SCR(chunk_counts, 20 * n * nch);
     SCR(totals, 8 * n);
@@ -362,11 +380,12 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
     P.chunk_pool = chunk_pool;
     P.brick_len = s->d_brick_len;
     P.chunk_counts = chunk_counts;
+    P.chunk_maxerr = chunk_maxerr;
     P.flags = flags;
     P.pool_used = used;
 
     std::vector<uint64_t> h_tot(n);
-    std::vector<unsigned long long> h_cnt(5 * n);
+    std::vector<unsigned long long> h_cnt(5 * n), h_merr(n);
     unsigned int h_flags = 0;
     unsigned long long h_used = 0;
     // the pool is shared by every call on this device: hold it until the
@@ -397,10 +416,12 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
       }
       if (e == cudaSuccess) {
         TimedLaunch tl(PC_KERNEL_SCAN, st);
-        e = launch_scan_chunks(chunk_nwords, s->d_chunk_word, totals, chunk_counts, counts, n, nch, st);
+        e = launch_scan_chunks(chunk_nwords, s->d_chunk_word, totals, chunk_counts, counts, chunk_maxerr, maxerr, n,
+                               nch, st);
       }
       if (e == cudaSuccess) e = cudaMemcpyAsync(h_tot.data(), totals, 8 * n, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt.data(), counts, 8 * 5 * n, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h_merr.data(), maxerr, 8 * n, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, flags, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h_used, used, 8, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -422,6 +443,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
         s->words[i] = h_tot[i];
         total += h_tot[i];
         for (int k = 0; k < 5; ++k) s->counts[i][k] = h_cnt[5 * i + k];
+        s->measured[i] = value_of_bits(h_merr[i], dtype);
       }
       e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
       if (e == cudaSuccess) e = cudaMemcpyAsync(comp_base, base.data(), 8 * n, cudaMemcpyHostToDevice, st);
@@ -438,6 +460,25 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
     return rc;
   }
   *out = s;
+  return PC_OK;
+}
+
+pc_status pc_query_k_measured(const pc_streams* s, double tau, int* k_out) {
+  g_err.clear();
+  if (!s || !k_out) return fail(PC_ERR_ARG, "NULL argument");
+  if (!(tau >= 0) || std::isnan(tau)) return fail(PC_ERR_ARG, "tau must be a number >= 0");
+  for (int i = 0; i < s->n; ++i)
+    if (s->measured[i] <= tau) {
+      *k_out = i + 1;
+      return PC_OK;
+    }
+  return fail(PC_ERR_TOL_UNREACHABLE, "tolerance finer than the last component's measured error");
+}
+
+pc_status pc_stream_measured_error(const pc_streams* s, int i, double* err) {
+  g_err.clear();
+  if (!s || !err || i < 0 || i >= s->n) return fail(PC_ERR_ARG, "bad streams, component index or pointer");
+  *err = s->measured[i];
   return PC_OK;
 }
 
@@ -534,10 +575,10 @@ pc_status pc_stream_device_ptrs(const pc_streams* s, int i, const uint64_t** pay
 
 // Serialized layout (little endian): a 64-byte header {magic, version, dtype,
 // ndims, n, 0, dims[3], nbricks, nchunks}, then per component {tau, words,
-// counts[5]} (56 bytes), then per component chunk_word[nchunks] (u64),
+// counts[5], measured error} (64 bytes), then per component chunk_word[nchunks] (u64),
 // brick_len[nbricks] (u16, padded to 8 bytes) and payload[words] (u64).
 static size_t serialized_size(const pc_streams* s) {
-  size_t sz = 64 + 56 * (size_t)s->n;
+  size_t sz = 64 + kCompRecord * (size_t)s->n;
   for (int i = 0; i < s->n; ++i)
     sz += 8 * (size_t)s->nchunks + (((size_t)s->nbricks * 2 + 7) & ~(size_t)7) + 8 * s->words[i];
   return sz;
@@ -565,7 +606,8 @@ pc_status pc_streams_serialize(const pc_streams* s, void* h_buf, size_t* len, vo
     std::memcpy(p, &s->tau[i], 8);
     std::memcpy(p + 8, &s->words[i], 8);
     std::memcpy(p + 16, s->counts[i], 40);
-    p += 56;
+    std::memcpy(p + 56, &s->measured[i], 8);
+    p += kCompRecord;
   }
   for (int i = 0; i < s->n; ++i) {
     CK(cudaMemcpyAsync(p, s->d_chunk_word + (int64_t)i * s->nchunks, 8 * s->nchunks, cudaMemcpyDeviceToHost, st));
@@ -613,7 +655,7 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
     return fail(PC_ERR_CORRUPT_STREAM, "brick counts do not match the extents");
   }
   size_t off = 64;
-  if (len < off + 56 * (size_t)n) {
+  if (len < off + kCompRecord * (size_t)n) {
     delete s;
     return fail(PC_ERR_CORRUPT_STREAM, "truncated");
   }
@@ -622,7 +664,8 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
     std::memcpy(&s->tau[i], p + off, 8);
     std::memcpy(&s->words[i], p + off + 8, 8);
     std::memcpy(s->counts[i], p + off + 16, 40);
-    off += 56;
+    std::memcpy(&s->measured[i], p + off + 56, 8);
+    off += kCompRecord;
     s->word_base[i] = total;
     total += s->words[i];
   }
@@ -630,6 +673,11 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
     delete s;
     return fail(PC_ERR_CORRUPT_STREAM, "bad tolerances");
   }
+  for (int i = 0; i < n; ++i)
+    if (!(s->measured[i] >= 0.0) || !std::isfinite(s->measured[i])) {
+      delete s;
+      return fail(PC_ERR_CORRUPT_STREAM, "bad measured errors");
+    }
   for (int i = 0; i < n; ++i) s->L[i] = floor_log2_bits(s->tau[i]);
   if (len != serialized_size(s)) {
     delete s;

@@ -52,7 +52,8 @@ constexpr size_t compress_smem3() {
          + (size_t)kChunk * 64 * 8             // plane words of every brick
          + (size_t)kChunk * 64 * 4             // plane code offsets and significance counts
          + 32 * 4 * 5                          // lengths, offsets, modes, escalations, violations
-         + 16;                                 // pool base
+         + 16                                  // pool base
+         + 32 * 8;                             // per brick: bits of max |x - x~_i|
 }
 
 // R11 group-test bits of one coefficient c that turns significant in plane
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
   int* s_esc = s_mode + 32;
   int* s_viol = s_esc + 32;
   unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_viol + 32);
+  uint64_t* s_merr = reinterpret_cast<uint64_t*>(s_base + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int h = lane >> 4, t = lane & 15;
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
     // (a RAW brick stores the current residual)
     T xtnew[4], enew[4];
     int viol = 0;  // Eq. 1 failures left (only a RAW brick can have them)
+    U merr = 0;    // max |x - x~_i| over this lane's in-field values, as bits (Sec. 4.3)
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       if (mode == kModeCoded) {
@@ -404,16 +407,25 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
         xtnew[m] = xt[m];
         enew[m] = e[m];
       }
-      if (line_in && m < nvx && !within<T>(enew[m], tb)) ++viol;
+      if (line_in && m < nvx) {
+        if (!within<T>(enew[m], tb)) ++viol;
+        const U a = F::bits(enew[m]) & F::ABS;
+        merr = a > merr ? a : merr;
+      }
     }
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) viol += __shfl_xor_sync(FULL, viol, o);
+    for (int o = 8; o >= 1; o >>= 1) {
+      viol += __shfl_xor_sync(FULL, viol, o);
+      const U y = (U)__shfl_xor_sync(FULL, (typename std::conditional<sizeof(U) == 8, unsigned long long, unsigned>::type)merr, o);
+      merr = y > merr ? y : merr;
+    }
 
     if (t == 0) {
       s_len[slot] = blen;
       s_mode[slot] = have ? mode : -1;
       s_esc[slot] = (have && mode == kModeCoded) ? esc : 0;
       s_viol[slot] = have ? viol : 0;
+      s_merr[slot] = have ? (uint64_t)merr : 0ull;
     }
     __syncthreads();
     if (warp == 0) {  // chunk layout: brick offsets, pool space, index entries
@@ -432,10 +444,13 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
       const unsigned cc = __popc(__ballot_sync(FULL, md == kModeCoded));
       const unsigned cr = __popc(__ballot_sync(FULL, md == kModeRaw));
       int se = s_esc[lane], sv = s_viol[lane];
+      unsigned long long me = s_merr[lane];
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
         se += __shfl_xor_sync(FULL, se, o);
         sv += __shfl_xor_sync(FULL, sv, o);
+        const unsigned long long y = __shfl_xor_sync(FULL, me, o);
+        me = y > me ? y : me;
       }
       if (lane == 0) {
         // pool space for the chunk; the atomic's result is first needed after
@@ -450,6 +465,7 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
         cnt[2] = cr;
         cnt[3] = (uint32_t)se;
         cnt[4] = (uint32_t)sv;
+        if (P.chunk_maxerr) P.chunk_maxerr[ci] = me;
       }
       const int64_t bb = chunk * kChunk + lane;
       if (bb < P.nbricks) {

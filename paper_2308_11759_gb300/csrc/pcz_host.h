@@ -26,6 +26,7 @@ struct pc_streams {
   uint64_t words[pcz::kMaxComponents] = {};      // payload words per component
   uint64_t word_base[pcz::kMaxComponents] = {};  // component's first word in d_payload
   uint64_t counts[pcz::kMaxComponents][5] = {};
+  double measured[pcz::kMaxComponents] = {};      // computed tolerance max |fl(x - x~_i)| (Sec. 4.3)
   uint64_t* d_payload = nullptr;     // all components back to back
   uint64_t* d_chunk_word = nullptr;  // [n][nchunks]
   uint16_t* d_brick_len = nullptr;   // [n][nbricks]

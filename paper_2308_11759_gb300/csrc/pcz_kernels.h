@@ -28,6 +28,7 @@ struct CompressParams {
   uint16_t* brick_len;           // [n][nbricks] bits of each brick
   uint32_t* brick_off;           // [n][nbricks] first bit of each brick within its chunk (may be null)
   uint32_t* chunk_counts;        // [n][nchunks][5] ZERO, CODED, RAW, escalations, Eq. 1 failures
+  uint64_t* chunk_maxerr;        // [n][nchunks] bits of max |fl(x - x~_i)| over the chunk (may be null)
   unsigned int* flags;           // bit 0 non-finite input, bit 1 pool too small
 };
 
@@ -82,7 +83,8 @@ cudaError_t launch_retrieve(int dtype, int ndims, const RetrieveParams& p, cudaS
 cudaError_t launch_compress_small(int dtype, int ndims, const CompressParams& p, cudaStream_t s);
 cudaError_t launch_retrieve_small(int dtype, int ndims, const RetrieveParams& p, cudaStream_t s);
 cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint64_t* totals,
-                               const uint32_t* chunk_counts, unsigned long long* counts, int n,
+                               const uint32_t* chunk_counts, unsigned long long* counts,
+                               const uint64_t* chunk_maxerr, unsigned long long* maxerr, int n,
                                int64_t nchunks, cudaStream_t s);
 cudaError_t launch_pack(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
                         const uint64_t* word_off, const uint64_t* comp_base, uint64_t* payload, int n,

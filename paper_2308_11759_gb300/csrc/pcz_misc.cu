@@ -1,7 +1,7 @@
 // pcz_misc.cu -- the memory-bound kernels around the fused coder:
 //  * k_scan_chunks: per component, exclusive prefix sum of the chunks' word
 //    counts (their place in the packed stream) and the component totals, plus
-//    the block-mode counters;
+//    the block-mode counters and the largest error (Sec. 4.3);
 //  * k_pack: copies every chunk from the scratch pool to its place in the
 //    component's stream (word aligned, so a plain copy);
 //  * k_range: min and max of a field (Sec. 5.1: tau_0 is the value range) and
@@ -23,17 +23,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __
                                                                uint64_t* __restrict__ totals,
                                                                const uint32_t* __restrict__ chunk_counts,
                                                                unsigned long long* __restrict__ counts,
+                                                               const uint64_t* __restrict__ chunk_maxerr,
+                                                               unsigned long long* __restrict__ maxerr,
                                                                int64_t nchunks) {
   __shared__ uint64_t warp_sums[32];
   __shared__ uint64_t carry_s;
   __shared__ unsigned long long cnt_s[5];
+  __shared__ unsigned long long merr_s;
   const int comp = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t* in = nwords + (int64_t)comp * nchunks;
   uint64_t* out = word_off + (int64_t)comp * nchunks;
   const uint32_t* cc = chunk_counts + (int64_t)comp * nchunks * 5;
   if (tid == 0) carry_s = 0;
   if (tid < 5) cnt_s[tid] = 0;
+  if (tid == 0) merr_s = 0;
   unsigned long long my_cnt[5] = {0, 0, 0, 0, 0};
+  unsigned long long my_merr = 0;
+  const uint64_t* me = chunk_maxerr ? chunk_maxerr + (int64_t)comp * nchunks : nullptr;
   __syncthreads();
   for (int64_t tile = 0; tile < nchunks; tile += (int64_t)kScanThreads * kScanItems) {
     const int64_t first = tile + (int64_t)tid * kScanItems;
@@ -47,6 +53,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __
       if (c < nchunks) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) my_cnt[k] += cc[c * 5 + k];
+        if (me) my_merr = me[c] > my_merr ? me[c] : my_merr;
       }
     }
     uint64_t incl = local;
@@ -81,8 +88,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) atomicAdd(&cnt_s[k], my_cnt[k]);
+  atomicMax(&merr_s, my_merr);
   __syncthreads();
   if (tid == 0) totals[comp] = carry_s;
+  if (tid == 0 && maxerr) maxerr[comp] = merr_s;
   if (tid < 5) counts[comp * 5 + tid] = cnt_s[tid];
 }
 
@@ -176,10 +185,12 @@ __global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, int64_t 
 }
 
 cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint64_t* totals,
-                               const uint32_t* chunk_counts, unsigned long long* counts, int n, int64_t nchunks,
+                               const uint32_t* chunk_counts, unsigned long long* counts,
+                               const uint64_t* chunk_maxerr, unsigned long long* maxerr, int n, int64_t nchunks,
                                cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_scan_chunks<<<n, kScanThreads, 0, s>>>(nwords, word_off, totals, chunk_counts, counts, nchunks);
+  k_scan_chunks<<<n, kScanThreads, 0, s>>>(nwords, word_off, totals, chunk_counts, counts, chunk_maxerr, maxerr,
+                                           nchunks);
   return cudaGetLastError();
 }
 

@@ -154,7 +154,8 @@ pc_status pc_compress_noalloc(const void* d_field, const int64_t* dims, int ndim
   // the flags and the pool's bump counter must start at zero on every call
   e = cudaMemsetAsync(flags, 0, 16, st);
   if (e == cudaSuccess) e = launch_compress(dtype, ndims, P, st);
-  if (e == cudaSuccess) e = launch_scan_chunks(chunk_nwords, d_chunk_word, totals, chunk_counts, counts, n, nchunks, st);
+  if (e == cudaSuccess) e = launch_scan_chunks(chunk_nwords, d_chunk_word, totals, chunk_counts, counts, nullptr, nullptr, n,
+                                                nchunks, st);
   unsigned int h_flags = 0;
   unsigned long long hc[5 * PC_MAX_COMPONENTS];
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_words, totals, 8 * (size_t)n, cudaMemcpyDeviceToHost, st);

@@ -265,13 +265,20 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress_small(const Compress
 #pragma unroll
       for (int k = 0; k < N; ++k) w.put((uint64_t)F::bits(e[k]), F::P);
     }
-    // x~ += x_i; count Eq. 1 failures left (RAW only)
+    // x~ += x_i; count Eq. 1 failures left (RAW only) and the largest error
+    // (Sec. 4.3: the computed tolerance)
     int viol = 0;
+    unsigned long long merr = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       if (mode == kModeCoded) xt[k] = xtn[k];
       if (mode == kModeRaw) xt[k] = F::add(xt[k], e[k]);
-      if (have && (k & 3) < nvx && (k >> 2) < nvy && !within<T>(F::sub(x[k], xt[k]), tb)) ++viol;
+      if (have && (k & 3) < nvx && (k >> 2) < nvy) {
+        const T r = F::sub(x[k], xt[k]);
+        if (!within<T>(r, tb)) ++viol;
+        const unsigned long long a = (unsigned long long)(F::bits(r) & F::ABS);
+        merr = a > merr ? a : merr;
+      }
     }
     const unsigned cz = __popc(__ballot_sync(FULL, have && mode == kModeZero));
     const unsigned cc = __popc(__ballot_sync(FULL, have && mode == kModeCoded));
@@ -281,6 +288,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress_small(const Compress
     for (int o = 16; o >= 1; o >>= 1) {
       se += __shfl_xor_sync(FULL, se, o);
       viol += __shfl_xor_sync(FULL, viol, o);
+      const unsigned long long y = __shfl_xor_sync(FULL, merr, o);
+      merr = y > merr ? y : merr;
     }
     if (have) {
       P.brick_len[(int64_t)i * P.nbricks + b] = (uint16_t)len;
@@ -303,6 +312,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress_small(const Compress
         cnt[2] = cr;
         cnt[3] = (uint32_t)se;
         cnt[4] = (uint32_t)viol;
+        if (P.chunk_maxerr) P.chunk_maxerr[ci] = merr;
       }
       base = __shfl_sync(FULL, base, 0);
       uint64_t* b64 = reinterpret_cast<uint64_t*>(cbuf);

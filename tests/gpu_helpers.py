@@ -7,7 +7,7 @@ import numpy as np
 
 def parse_serialized(data: bytes):
     """Returns dict(dtype, ndims, dims, n, nbricks, nchunks, comps=[{tau, words,
-    counts, chunk_word, brick_len, payload}])."""
+    counts, measured, chunk_word, brick_len, payload}])."""
     magic, version, dtype, ndims, n, _ = struct.unpack_from("<6I", data, 0)
     dims = struct.unpack_from("<3q", data, 24)
     nbricks, nchunks = struct.unpack_from("<2q", data, 48)
@@ -16,8 +16,9 @@ def parse_serialized(data: bytes):
     for i in range(n):
         tau, words = struct.unpack_from("<dQ", data, off)
         counts = list(struct.unpack_from("<5Q", data, off + 16))
-        comps.append(dict(tau=tau, words=words, counts=counts))
-        off += 56
+        (measured,) = struct.unpack_from("<d", data, off + 56)
+        comps.append(dict(tau=tau, words=words, counts=counts, measured=measured))
+        off += 64
     for i in range(n):
         c = comps[i]
         c["chunk_word"] = np.frombuffer(data, dtype=np.uint64, count=nchunks, offset=off).copy()

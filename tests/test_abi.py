@@ -1,0 +1,81 @@
+"""The C ABI without a GPU: libpcz.so builds and loads, exports every function
+include/pcz.h declares, the ctypes structures have the header's sizes, and
+calls whose arguments are invalid fail with PC_ERR_ARG before any device work."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pcz.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2308_11759_gb300 import build as B
+
+    try:
+        B.build()
+    except (RuntimeError, FileNotFoundError) as e:  # no CUDA toolkit on this machine
+        pytest.skip(f"libpcz cannot be built here: {e}")
+    import paper_2308_11759_gb300 as P
+
+    return P.lib()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("pc_compress", "pc_retrieve", "pc_refine", "pc_query_k", "pc_query_k_measured",
+                 "pc_stream_measured_error", "pc_streams_serialize", "pc_streams_deserialize", "pc_server_create",
+                 "pc_server_replay", "pc_compress_noalloc", "pc_last_error", "pc_version"):
+        assert want in names
+
+
+def test_every_declared_function_is_exported(L):
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_struct_sizes(L):
+    import paper_2308_11759_gb300 as P
+
+    assert C.sizeof(P.Box) == 48
+    assert C.sizeof(P.Query) == 64  # int, int, double, pc_box
+    assert C.sizeof(P.ServeStats) == 56
+
+
+def test_version_and_error_text(L):
+    assert L.pc_version() == 2
+    assert isinstance(L.pc_last_error(), bytes)
+
+
+def test_argument_errors_without_device_work(L):
+    import paper_2308_11759_gb300 as P
+
+    k = C.c_int()
+    assert L.pc_query_k(None, 1.0, C.byref(k)) == 1
+    assert b"NULL" in L.pc_last_error()
+    assert L.pc_query_k_measured(None, 1.0, C.byref(k)) == 1
+    e = C.c_double()
+    assert L.pc_stream_measured_error(None, 0, C.byref(e)) == 1
+    h = C.c_void_p()
+    dims = (C.c_int64 * 3)(4, 4, 4)
+    tau = (C.c_double * 1)(1.0)
+    assert L.pc_compress(None, dims, 3, 1, tau, 1, None, C.byref(h)) == 1
+    assert L.pc_compress(None, dims, 3, 1, tau, 1, None, None) == 1
+    srv = C.c_void_p()
+    assert L.pc_server_create(1 << 30, 0, 0, None, C.byref(srv)) == 1  # max_batch < 1
+    assert L.pc_server_create(1 << 30, 4, 8, None, C.byref(srv)) == 1  # unknown flag
+    assert L.pc_server_free(None) == 0
+    st = C.c_void_p()
+    assert L.pc_streams_deserialize(None, 0, None, C.byref(st)) == 1
+    buf = (C.c_ubyte * 16)()
+    assert L.pc_streams_deserialize(buf, 16, None, C.byref(st)) == 8  # PC_ERR_VERSION: too short
+    assert P.STATUS[8] == "PC_ERR_VERSION"

@@ -1,0 +1,184 @@
+"""The C ABI on the GPU beyond the coder's bits: computed tolerances (Sec. 4.3)
+equal the oracle's, the query on them, serialization round trips and the
+checks on corrupt data, host-buffer calls, and every error status."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth_fields as S
+from tests.gpu_helpers import parse_serialized
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2308_11759_gb300 as pcz
+
+    pcz.lib()
+    return pcz
+
+
+CASES = [
+    ("pl3d_f32", lambda: S.powerlaw((40, 36, 33), seed=31, dtype=np.float32), 8),
+    ("fronts3d_f64", lambda: S.fronts((24, 20, 28), seed=32), 12),
+    ("pl2d_f64", lambda: S.powerlaw((70, 51), seed=33, dtype=np.float64), 8),
+    ("pl1d_f32", lambda: S.powerlaw((999,), seed=34, dtype=np.float32), 6),
+    ("lossless3d_f64", lambda: _in_6_14(S.powerlaw((12, 10, 9), seed=21, dtype=np.float64)), 16),
+]
+
+
+def _in_6_14(f):
+    """values in [6, 14]: the binary schedule's last tolerances lie below every ulp."""
+    return 10.0 + 4.0 * f / np.abs(f).max()
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def pair(request, P):
+    _, make, n = request.param
+    x = np.ascontiguousarray(make())
+    tau = O.tau_binary(O.value_range(x), 4, n) if "lossless" in request.param[0] else \
+        O.tau_decade(O.value_range(x), n, first_exp=1)
+    st = P.compress(torch.from_numpy(x).cuda(), tau)
+    return x, tau, st, O.Streams(x, tau, nthreads=4)
+
+
+def test_measured_errors_equal_oracle(pair):
+    x, tau, st, ref = pair
+    for i in range(st.n):
+        m = st.measured_error(i)
+        assert m == ref.measured(i), i
+        assert m <= tau[i]
+        got = st.retrieve(k=i + 1).cpu().numpy()
+        assert m == float(np.max(np.abs(np.subtract(x, got, dtype=x.dtype))))
+
+
+def test_query_on_measured_errors(pair):
+    x, tau, st, ref = pair
+    meas = [st.measured_error(i) for i in range(st.n)]
+    rng = np.random.default_rng(8)
+    for t in tau[0] * 10.0 ** (-rng.uniform(0.0, 14.0, 30)):
+        if t < min(meas):
+            with pytest.raises(Exception):
+                st.query_k(t, measured=True)
+            continue
+        k = st.query_k(t, measured=True)
+        assert k == O.query_k(meas, t)
+        if t >= tau[-1]:
+            assert k <= st.query_k(t)
+
+
+def test_lossless_where_measured_error_is_zero(P):
+    x = _in_6_14(S.powerlaw((12, 10, 9), seed=21, dtype=np.float64))
+    tau = O.tau_binary(O.value_range(x), 4, 16)
+    st = P.compress(torch.from_numpy(x).cuda(), tau)
+    meas = [st.measured_error(i) for i in range(st.n)]
+    k0 = next(i + 1 for i, m in enumerate(meas) if m == 0.0)
+    assert torch.equal(st.retrieve(k=k0).cpu().view(torch.uint8), torch.from_numpy(x).view(torch.uint8))
+    assert st.query_k(0.0, measured=True) == k0
+
+
+def test_serialize_round_trip(P, pair):
+    x, tau, st, ref = pair
+    blob = st.serialize()
+    d = parse_serialized(blob)
+    assert d["version"] == 2
+    for i in range(st.n):
+        assert d["comps"][i]["measured"] == st.measured_error(i)
+    st2 = P.Streams.deserialize(blob)
+    assert st2.shape == st.shape and st2.n == st.n
+    assert st2.serialize() == blob
+    for k in (1, st.n):
+        assert torch.equal(st2.retrieve(k=k).view(torch.uint8), st.retrieve(k=k).view(torch.uint8))
+    for i in range(st.n):
+        assert st2.measured_error(i) == st.measured_error(i)
+        assert st2.counts(i) == st.counts(i)
+
+
+def _status(fn):
+    with pytest.raises(Exception) as e:
+        fn()
+    return getattr(e.value, "name", None)
+
+
+def test_corrupt_streams_are_rejected(P, pair):
+    x, tau, st, ref = pair
+    blob = bytearray(st.serialize())
+    bad = bytearray(blob)
+    bad[4] = 1  # format version 1
+    assert _status(lambda: P.Streams.deserialize(bytes(bad))) == "PC_ERR_VERSION"
+    bad = bytearray(blob)
+    bad[0] ^= 0xFF  # magic
+    assert _status(lambda: P.Streams.deserialize(bytes(bad))) == "PC_ERR_VERSION"
+    assert _status(lambda: P.Streams.deserialize(bytes(blob[:-8]))) == "PC_ERR_CORRUPT_STREAM"
+    d = parse_serialized(bytes(blob))
+    n, nch, nbr = d["n"], d["nchunks"], d["nbricks"]
+    # the first brick length of component 1 made one bit longer: its block no longer parses
+    bl_off = 64 + 64 * n + 8 * nch
+    bad = bytearray(blob)
+    v = int.from_bytes(bad[bl_off:bl_off + 2], "little")
+    bad[bl_off:bl_off + 2] = (v + 1).to_bytes(2, "little")
+    assert _status(lambda: P.Streams.deserialize(bytes(bad))) == "PC_ERR_CORRUPT_STREAM"
+    bad = bytearray(blob)
+    bad[64 + 56:64 + 64] = np.float64(-1.0).tobytes()  # a negative measured error
+    assert _status(lambda: P.Streams.deserialize(bytes(bad))) == "PC_ERR_CORRUPT_STREAM"
+    bad = bytearray(blob)
+    bad[64:72] = np.float64(tau[1]).tobytes() if n > 1 else np.float64(-1.0).tobytes()  # tau no longer decreasing
+    assert _status(lambda: P.Streams.deserialize(bytes(bad))) == "PC_ERR_CORRUPT_STREAM"
+
+
+def test_host_buffers(P):
+    x = S.powerlaw((21, 19, 17), seed=35, dtype=np.float32)
+    tau = O.tau_decade(O.value_range(x), 5)
+    dev = P.compress(torch.from_numpy(x).cuda(), tau)
+    host = P.compress(x, tau)  # the library copies the field in
+    assert host.serialize() == dev.serialize()
+    out = np.empty_like(x)
+    host.retrieve(k=3, out=out)
+    assert np.array_equal(out.view(np.uint8), dev.retrieve(k=3).cpu().numpy().view(np.uint8))
+    part = np.empty((5, 6, 7), dtype=np.float32)
+    host.retrieve(k=4, box=([3, 2, 1], [8, 8, 8]), out=part)
+    assert np.array_equal(part, dev.retrieve(k=4).cpu().numpy()[3:8, 2:8, 1:8])
+
+
+def test_error_statuses(P):
+    x = S.powerlaw((9, 8, 7), seed=36, dtype=np.float64)
+    xd = torch.from_numpy(x).cuda()
+    tau = [0.1, 0.01, 0.001]
+    for bad_val in (np.nan, np.inf, -np.inf):
+        y = x.copy()
+        y[4, 3, 2] = bad_val
+        assert _status(lambda: P.compress(torch.from_numpy(y).cuda(), tau)) == "PC_ERR_NONFINITE"
+    assert _status(lambda: P.compress(xd, [0.1, 0.2])) == "PC_ERR_TAU_ORDER"
+    assert _status(lambda: P.compress(xd, [0.1, 0.0])) == "PC_ERR_TAU_ORDER"
+    assert _status(lambda: P.compress(xd, [0.1, float("nan")])) == "PC_ERR_TAU_ORDER"
+    assert _status(lambda: P.compress(xd, [])) == "PC_ERR_ARG"
+    st = P.compress(xd, tau)
+    assert _status(lambda: st.query_k(1e-4)) == "PC_ERR_TOL_UNREACHABLE"
+    assert _status(lambda: st.retrieve(tau=1e-4)) == "PC_ERR_TOL_UNREACHABLE"
+    assert _status(lambda: st.retrieve(k=4)) == "PC_ERR_ARG"
+    assert _status(lambda: st.retrieve(k=1, box=([0, 0, 0], [10, 8, 7]))) == "PC_ERR_ARG"
+    assert _status(lambda: st.retrieve(k=1, box=([3, 0, 0], [3, 8, 7]))) == "PC_ERR_ARG"
+    assert _status(lambda: st.refine(2, 1, torch.empty_like(xd))) == "PC_ERR_ARG"
+    assert st.query_k(0.5) == 1 and st.query_k(0.01) == 2
+    z = st.retrieve(k=0).cpu().numpy()
+    assert not z.any()
+
+
+def test_lossless_sweep(P):
+    """Sec. 5.1.3 on a float32 and a float64 field: the sweep's k reproduces x
+    bit for bit, k - 1 does not, and the rate is the streams' own."""
+    for dt, shape in ((np.float32, (20, 18, 16)), (np.float64, (48, 40))):
+        x = S.powerlaw(shape, seed=37, dtype=dt)
+        xd = torch.from_numpy(x).cuda()
+        r = P.lossless_sweep(xd, delta=4)
+        k, st = r["k"], r["streams"]
+        assert k is not None
+        assert torch.equal(st.retrieve(k=k).view(torch.uint8), xd.view(torch.uint8))
+        assert not torch.equal(st.retrieve(k=k - 1), xd)
+        bits = sum(st.info(i)[1] + 8 * st.info(i)[2] for i in range(k)) / x.size
+        assert r["bits_per_value"] == bits and r["ratio"] == 8 * x.itemsize / bits
+        ref = O.Streams(x, [st.tau(i) for i in range(st.n)], nthreads=4)
+        assert [ref.measured(i) for i in range(st.n)] == r["measured"]
