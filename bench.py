@@ -16,7 +16,10 @@ every retrieval is written back to host memory.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pcz|reference]
 
-The line also carries `serving`: the progressive-query workload (16 float32
+The line also carries `batched`: the uneven batch of 64 float32 fields (half
+2D, half 3D, 6 components) compressed by one graph-replayed persistent launch
+and retrieved by one launch per dimensionality, against per-field calls; and
+`serving`: the progressive-query workload (16 float32
 256^3 k^-5/3 fields resident on the device, 8 components each; 10,000 seeded
 queries arriving as a Poisson stream at 2,000/s, each a brick-aligned sub-box
 with sides log-uniform in [8, 256] at a relative tolerance log-uniform in
@@ -46,6 +49,9 @@ sys.path.insert(0, ROOT)
 
 N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
+BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
+                  "384x384x256 (not multiples of 4), half sums of Gaussians and half k^-5/3 spectra, 6 components "
+                  "(tau_i = 1e-(i+1) * range)")
 SERVE_WORKLOAD = ("16 device-resident float32 256^3 k^-5/3 fields, 8 components (tau_i = 1e-(i+1) * range); "
                   "Poisson arrivals at 2000/s; brick-aligned sub-boxes with sides log-uniform in [8, 256]; "
                   "relative tolerance log-uniform in [1e-7, 1e-1]; 20 GB budget")
@@ -353,6 +359,85 @@ def run_serving(args, device):
     return out
 
 
+def run_batched(args, device):
+    """The uneven batch: one graph-replayed persistent launch for all 64
+    fields against a loop of per-field compress calls; batched retrieval of
+    every field at k = 6 against per-field retrievals."""
+    import torch
+
+    import paper_2308_11759_gb300 as pcz
+    import synth_fields as S
+
+    shapes = S.batched_shapes(64, seed=3)
+    fields = []
+    for j, sh in enumerate(shapes):
+        if (j // 2) % 2 == 0:
+            fields.append(S.gaussians(sh, seed=200 + j, dtype=np.float32, device=device).contiguous())
+        else:
+            fields.append(S.powerlaw(sh, seed=200 + j, dtype=np.float32, device=device).contiguous())
+    taus = []
+    for x in fields:
+        lo, hi = pcz.field_range(x)
+        taus.append(pcz.tau_decade(hi - lo, 6))
+    torch.cuda.synchronize()
+    raw = sum(x.numel() * 4 for x in fields)
+    plan = pcz.Batch(shapes, np.float32, 6)
+    t_tune = time.perf_counter()
+    for st in plan.compress(fields, taus):  # first call: the autotuner times its schedules
+        st.close()
+    t_tune = time.perf_counter() - t_tune
+    reps = max(2, args.steps)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def batched():
+        for st in plan.compress(fields, taus):
+            st.close()
+
+    def loop():
+        for x, t in zip(fields, taus):
+            pcz.compress(x, t).close()
+
+    ms_b = timed(batched)
+    ms_l = timed(loop)
+    sts = plan.compress(fields, taus)
+    outs = [torch.empty_like(x) for x in fields]
+    ms_rb = timed(lambda: pcz.retrieve_batch(sts, [6] * len(sts), outs=outs))
+
+    def rloop():
+        for st, o in zip(sts, outs):
+            st.retrieve(k=6, out=o)
+
+    ms_rl = timed(rloop)
+    bits = sum(st.info(i)[1] for st in sts for i in range(6)) / (raw / 4)
+    for st in sts:
+        st.close()
+    info = plan.info()
+    plan.close()
+    return {"workload": BATCH_WORKLOAD, "fields": len(shapes), "raw_bytes": raw,
+            "compress": {"batched_gbs": round(raw / (ms_b * 1e-3) / 1e9, 3), "batched_ms": round(ms_b, 3),
+                         "per_field_loop_gbs": round(raw / (ms_l * 1e-3) / 1e9, 3),
+                         "per_field_loop_ms": round(ms_l, 3)},
+            "retrieve_k6": {"batched_gbs": round(raw / (ms_rb * 1e-3) / 1e9, 3), "batched_ms": round(ms_rb, 3),
+                            "per_field_loop_gbs": round(raw / (ms_rl * 1e-3) / 1e9, 3),
+                            "per_field_loop_ms": round(ms_rl, 3)},
+            "bits_per_value": round(bits, 3),
+            "autotuner": {"schedule": info["schedule"], "order": info["order"],
+                          "chunks_per_item": info["chunks_per_item"], "items_per_claim": info["items_per_claim"],
+                          "candidate_ms": [round(v, 3) for v in info["candidate_ms"]],
+                          "first_call_s": round(t_tune, 3)},
+            "graph": bool(info["graph"]), "timing": "CUDA events around whole calls (host work included)"}
+
+
 def run_lossless(device):
     """Sec. 5.1.3 on synthetic fields: components (binary schedule, delta = 4,
     8 and 16) until the computed tolerance is 0, the bits per value that takes
@@ -418,6 +503,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-lossless", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=10000)
     ap.add_argument("--serve-size", type=int, default=256)
     args = ap.parse_args()
@@ -463,6 +549,7 @@ def main():
         torch.cuda.empty_cache()
         serving = run_serving(args, device)
     lossless = None if args.no_lossless else run_lossless(device)
+    batched = None if args.no_batched else run_batched(args, device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -495,6 +582,7 @@ def main():
             "rates_bits_per_value": {k: v["rates"] for k, v in r["info"].items()},
             "computed_tolerances": {k: v["measured_over_tau"] for k, v in r["info"].items()},
             "lossless": lossless,
+            "batched": batched,
             "serving": serving,
         }
         print(json.dumps(line))

@@ -309,6 +309,63 @@ pc_status pc_server_reset_cache(pc_server *srv);
 /* Releases the server and its device memory (not the streams).  NULL is a no-op. */
 pc_status pc_server_free(pc_server *srv);
 
+/*
+ * Batched construction (Algorithm 1 over many fields at once).  A plan fixes
+ * the fields' shapes, the type and the number of components; each
+ * pc_batch_compress call then codes one set of fields of those shapes (new
+ * values and tolerances) in one persistent kernel launch over all the
+ * fields' chunks -- 3D chunks by whole CTAs, 1D/2D chunks by single warps --
+ * followed by one segmented scan (per field and component) and one packing
+ * launch.  The launches up to the scan are captured in a CUDA graph when the
+ * plan is created and replayed on every call.  On the plan's first call an
+ * autotuner times a fixed set of schedules (field order, chunks per work
+ * item, items per claim) on that batch and keeps the fastest
+ * (pc_batch_info).  The result of every call is exactly what pc_compress
+ * gives for each field on its own, bit for bit.
+ *
+ *   pc_batch_create: nfields >= 1; dims: 3 extents per field (x first,
+ *     entries beyond the field's ndims ignored); ndims: 1..3 per field; n
+ *     components for every field.  The plan runs on a stream of its own and
+ *     each call first waits for the work queued on cuda_stream.
+ *   pc_batch_compress: d_fields: nfields device pointers (dense, x fastest);
+ *     tau: n tolerances per field, field after field; out: nfields
+ *     pc_streams* (freed one by one with pc_streams_free; the batch's
+ *     device arrays are released with the last of them).  Errors as
+ *     pc_compress (PC_ERR_TAU_ORDER, PC_ERR_NONFINITE, ...).  Synchronises
+ *     the plan's stream.
+ */
+typedef struct pc_batch pc_batch; /* opaque */
+
+typedef struct {
+  int schedule;          /* index of the chosen schedule, -1 before the first call */
+  int order;             /* 0: fields in the given order, 1: largest first */
+  int chunks_per_item;   /* chunks of a 1D/2D field per work item */
+  int items_per_claim;   /* work items a CTA claims per atomic */
+  int candidates;        /* schedules timed by the autotuner */
+  int grid;              /* persistent CTAs */
+  int graph;             /* 1 when the launches run as a CUDA graph */
+  int pad_;
+  uint64_t calls;        /* pc_batch_compress calls so far */
+  double candidate_ms[16]; /* the autotuner's timings (ms) */
+} pc_batch_info_t;
+
+pc_status pc_batch_create(int nfields, const int64_t *dims, const int *ndims, pc_dtype dtype, int n,
+                          void *cuda_stream, pc_batch **out);
+pc_status pc_batch_compress(pc_batch *b, const void *const *d_fields, const double *tau, pc_streams **out);
+pc_status pc_batch_info(const pc_batch *b, pc_batch_info_t *info);
+pc_status pc_batch_free(pc_batch *b);
+
+/*
+ * Batched retrieval (Algorithm 2 over many boxes at once): query q returns
+ * x~_{k[q]} of streams s[q] on boxes[q] (NULL boxes: whole fields) into the
+ * device buffer d_out[q] (box values, x fastest).  The queries of each type
+ * and dimensionality run in one launch of the retrieval kernel over a list
+ * of box jobs.  Same results as pc_retrieve per query.  Asynchronous on
+ * cuda_stream.
+ */
+pc_status pc_retrieve_batch(int nq, const pc_streams *const *s, const int *k, const pc_box *boxes,
+                            void *const *d_out, void *cuda_stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *pc_last_error(void);
 

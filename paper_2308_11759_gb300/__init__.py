@@ -50,6 +50,12 @@ class ServeStats(C.Structure):
 PC_SERVE_NO_CACHE, PC_SERVE_SERIAL = 1, 2
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("schedule", C.c_int), ("order", C.c_int), ("chunks_per_item", C.c_int),
+                ("items_per_claim", C.c_int), ("candidates", C.c_int), ("grid", C.c_int), ("graph", C.c_int),
+                ("pad_", C.c_int), ("calls", C.c_uint64), ("candidate_ms", C.c_double * 16)]
+
+
 _lib = None
 
 
@@ -79,6 +85,11 @@ def lib():
             "pc_stream_read_index": [vp, C.c_int, u64p, C.POINTER(C.c_uint16), vp],
             "pc_stream_read": [vp, C.c_int, C.c_uint64, C.c_uint64, u64p, vp],
             "pc_server_create": [C.c_uint64, C.c_int, C.c_int, vp, C.POINTER(vp)],
+            "pc_batch_create": [C.c_int, i64p, ip, C.c_int, C.c_int, vp, C.POINTER(vp)],
+            "pc_batch_compress": [vp, C.POINTER(vp), dp, C.POINTER(vp)],
+            "pc_batch_info": [vp, C.POINTER(BatchInfo)],
+            "pc_batch_free": [vp],
+            "pc_retrieve_batch": [C.c_int, C.POINTER(vp), ip, C.POINTER(Box), C.POINTER(vp), vp],
             "pc_server_add_field": [vp, vp, ip],
             "pc_server_replay": [vp, C.POINTER(Query), dp, C.c_int, C.POINTER(vp), dp, C.POINTER(ServeStats)],
             "pc_server_reset_cache": [vp],
@@ -300,6 +311,88 @@ class Streams:
         buf = C.create_string_buffer(n.value)
         _check(lib().pc_streams_serialize(self._h, buf, C.byref(n), _stream_ptr(stream)))
         return buf.raw[: n.value]
+
+
+class Batch:
+    """A plan for compressing many fields of fixed shapes at once (pc_batch_*):
+    one persistent launch over all fields' chunks, replayed as a CUDA graph,
+    schedule picked by an autotuner on the first call."""
+
+    def __init__(self, shapes, dtype, n: int, stream=None):
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.dtype = dtype
+        self.n = int(n)
+        nf = len(self.shapes)
+        dims = (C.c_int64 * (3 * nf))()
+        nds = (C.c_int * nf)()
+        for f, sh in enumerate(self.shapes):
+            rev = list(sh[::-1]) + [1] * (3 - len(sh))
+            for a in range(3):
+                dims[3 * f + a] = rev[a]
+            nds[f] = len(sh)
+        self._h = C.c_void_p()
+        _check(lib().pc_batch_create(nf, dims, nds, _dtype_code(dtype), self.n, _stream_ptr(stream),
+                                     C.byref(self._h)))
+
+    def compress(self, fields, taus):
+        """fields: CUDA tensors of the plan's shapes; taus: one list of n
+        tolerances per field.  Returns one Streams per field."""
+        nf = len(self.shapes)
+        if len(fields) != nf or len(taus) != nf:
+            raise ValueError("one field and one tolerance list per planned shape")
+        for x, sh in zip(fields, self.shapes):
+            if tuple(x.shape) != sh:
+                raise ValueError(f"field of shape {tuple(x.shape)} where {sh} was planned")
+        ptrs = (C.c_void_p * nf)(*[_ptr(x).value for x in fields])
+        flat = [float(t) for tl in taus for t in tl]
+        if len(flat) != nf * self.n:
+            raise ValueError("n tolerances per field")
+        tau = (C.c_double * len(flat))(*flat)
+        outs = (C.c_void_p * nf)()
+        _check(lib().pc_batch_compress(self._h, ptrs, tau, outs))
+        torch = _torch()
+        tdt = torch.float32 if _dtype_code(self.dtype) == PC_F32 else torch.float64
+        return [Streams(C.c_void_p(outs[f]), self.shapes[f], tdt) for f in range(nf)]
+
+    def info(self):
+        inf = BatchInfo()
+        _check(lib().pc_batch_info(self._h, C.byref(inf)))
+        d = {name: getattr(inf, name) for name, _ in BatchInfo._fields_ if name not in ("pad_", "candidate_ms")}
+        d["candidate_ms"] = [inf.candidate_ms[i] for i in range(inf.candidates)]
+        return d
+
+    def close(self):
+        if self._h:
+            lib().pc_batch_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def retrieve_batch(streams, ks, boxes=None, outs=None, stream=None):
+    """Algorithm 2 for many (streams, k, box) queries in one launch per type
+    and dimensionality (pc_retrieve_batch).  Returns the output tensors."""
+    torch = _torch()
+    nq = len(streams)
+    bx = (Box * max(nq, 1))()
+    res = []
+    for q in range(nq):
+        st = streams[q]
+        box = boxes[q] if boxes is not None else None
+        b, ext = _box(box, st.shape)
+        if b is None:
+            b, ext = _box(([0] * len(st.shape), list(st.shape)), st.shape)
+        bx[q] = b
+        res.append(outs[q] if outs is not None else torch.empty(ext, dtype=st.dtype, device="cuda"))
+    sp = (C.c_void_p * max(nq, 1))(*[st._h.value for st in streams])
+    kk = (C.c_int * max(nq, 1))(*[int(k) for k in ks])
+    op = (C.c_void_p * max(nq, 1))(*[o.data_ptr() for o in res])
+    _check(lib().pc_retrieve_batch(nq, sp, kk, bx, op, _stream_ptr(stream)))
+    return res
 
 
 class Server:

@@ -13,8 +13,8 @@ import tempfile
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpcz.so")
-SOURCES = ["pcz_api.cu", "pcz_compress.cu", "pcz_retrieve.cu", "pcz_misc.cu", "pcz_noalloc.cu", "pcz_small.cu", "pcz_serve.cu"]
-HEADERS = ["pcz_device.cuh", "pcz_kernels.h", "pcz_host.h", os.path.join("..", "..", "include", "pcz.h")]
+SOURCES = ["pcz_api.cu", "pcz_compress.cu", "pcz_retrieve.cu", "pcz_misc.cu", "pcz_noalloc.cu", "pcz_small.cu", "pcz_serve.cu", "pcz_batch.cu"]
+HEADERS = ["pcz_device.cuh", "pcz_kernels.h", "pcz_host.h", "pcz_chunk3.cuh", "pcz_chunk_small.cuh", os.path.join("..", "..", "include", "pcz.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-fmad=false", "-ftz=false",

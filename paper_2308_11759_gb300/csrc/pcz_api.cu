@@ -109,7 +109,7 @@ uint64_t tau_threshold_bits(double tau, pc_dtype dt) {
 }
 
 // The T value of a bit pattern, as a double (exact).
-double value_of_bits(uint64_t b, pc_dtype dt) {
+double bits_to_double(uint64_t b, pc_dtype dt) {
   if (dt == PC_F64) {
     double d;
     std::memcpy(&d, &b, 8);
@@ -180,12 +180,14 @@ namespace {
 void streams_release(pc_streams* s) {
   if (!s) return;
   cudaDeviceSynchronize();
-  cudaFree(s->d_payload);
-  cudaFree(s->d_chunk_word);
-  cudaFree(s->d_brick_len);
-  cudaFree(s->d_brick_off);
-  cudaFree(s->d_desc);
-  cudaFree(s->d_err);
+  if (!s->backing) {  // a batch's streams share device arenas, freed with the last of them
+    cudaFree(s->d_payload);
+    cudaFree(s->d_chunk_word);
+    cudaFree(s->d_brick_len);
+    cudaFree(s->d_brick_off);
+    cudaFree(s->d_desc);
+    cudaFree(s->d_err);
+  }
   delete s;
 }
 
@@ -282,6 +284,15 @@ BoxJob pcz::make_box_job(const pc_streams* s, int k0, int k, const int64_t lo[3]
   return make_job(s, k0, k, lo, hi, out);
 }
 int64_t pcz::box_job_units(const BoxJob& J) { return job_units(J); }
+double pcz::value_of_bits(uint64_t b, pc_dtype dt) { return bits_to_double(b, dt); }
+int pcz::floor_log2_of(double tau) { return floor_log2_bits(tau); }
+uint64_t pcz::tau_bits_of(double tau, pc_dtype dt) { return tau_threshold_bits(tau, dt); }
+bool pcz::tolerances_valid(const double* tau, int n) { return tau_valid(tau, n); }
+void pcz::field_geometry(int ndims, const int64_t* dims, int64_t d3[3], int64_t nb[3], int64_t* nbricks,
+                         int64_t* nchunks) {
+  make_geometry(ndims, dims, d3, nb, nbricks, nchunks);
+}
+bool pcz::device_pointer(const void* p) { return is_device_ptr(p); }
 
 extern "C" {
 
@@ -443,7 +454,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
         s->words[i] = h_tot[i];
         total += h_tot[i];
         for (int k = 0; k < 5; ++k) s->counts[i][k] = h_cnt[5 * i + k];
-        s->measured[i] = value_of_bits(h_merr[i], dtype);
+        s->measured[i] = bits_to_double(h_merr[i], dtype);
       }
       e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
       if (e == cudaSuccess) e = cudaMemcpyAsync(comp_base, base.data(), 8 * n, cudaMemcpyHostToDevice, st);

@@ -20,525 +20,14 @@
 // coefficients.  The chunk's bits are assembled in shared memory and appended to
 // a scratch pool with one atomic per chunk; pcz_misc.cu then scans the chunk
 // sizes and packs the final streams.
-#include <climits>
-#include <type_traits>
-
-#include "pcz_device.cuh"
-#include "pcz_kernels.h"
+#include "pcz_chunk3.cuh"
 
 namespace pcz {
 
-__constant__ PermTable kPerm3 = make_perm(64);
-
-// Largest bit string of one brick and component: CODED with every plane
-// non-empty (each plane at most 2N + 1 bits) plus the header.
-template <typename T>
-__host__ __device__ constexpr int max_brick_bits3() {
-  return 2 + 3 + Fmt<T>::EBITS + Fmt<T>::P * (2 * 64 + 1);
-}
-
-template <typename T>
-__host__ __device__ constexpr int chunk_buf_words3() {  // u32 words, rounded to whole u64 words
-  return ((kChunk * max_brick_bits3<T>() + 63) / 64) * 2;
-}
-
-constexpr int kCompressThreads3 = 512;
-
-template <typename T>
-constexpr size_t compress_smem3() {
-  using S = typename Fmt<T>::S;
-  return (size_t)chunk_buf_words3<T>() * 4      // chunk bit buffer
-         + (size_t)kChunk * 64 * sizeof(S)     // brick buffers, 128 elements per warp
-         + (size_t)kChunk * 64 * 8             // plane words of every brick
-         + (size_t)kChunk * 64 * 4             // plane code offsets and significance counts
-         + 32 * 4 * 5                          // lengths, offsets, modes, escalations, violations
-         + 16                                  // pool base
-         + 32 * 8;                             // per brick: bits of max |x - x~_i|
-}
-
-// R11 group-test bits of one coefficient c that turns significant in plane
-// pc (its highest set bit, at or above the lowest coded plane): when n
-// coefficients are significant before pc and c >= n, c is a token of that
-// plane.  With k its rank among the plane's tokens (1-based), the group part
-// of the plane (which follows the n verbatim bits) holds c's 1 at c - n + k,
-// the next token's test bit right after it unless c is the plane's last
-// token, and the plane's first test bit at 0 (set by the token with k = 1).
-// Zeros (runs and the closing test bit) need no write.
-__device__ __forceinline__ void write_token(uint32_t* buf, uint32_t group_base, uint64_t W, int n, int c) {
-  const uint64_t before = W & low_mask64(c) & ~low_mask64(n);
-  const int k = 1 + __popcll((long long)before);
-  const bool last = c >= 63 || (W >> (c + 1)) == 0ull;
-  or_bits(buf, group_base + (uint32_t)(c - n + k), last ? 1ull : 3ull);
-  if (k == 1) atomicOr(buf + (group_base >> 5), 1u << (group_base & 31));
-}
-
-// Suffix scans of one round of 32 planes (lane l = plane base + l, coded in
-// descending order): n before each plane (max of the one-past-highest set
-// position over the planes above) and the plane's bit offset.
-template <int N>
-__device__ __forceinline__ void plane_scan(uint64_t W, bool act, int lane, int& cmax, int& csum, int& n_out,
-                                           int& off_out) {
-  constexpr unsigned FULL = 0xffffffffu;
-  const int hi = (act && W) ? 64 - __clzll((long long)W) : 0;
-  int v = hi;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_down_sync(FULL, v, o);
-    if (lane + o < 32) v = max(v, y);
-  }
-  int ex = __shfl_down_sync(FULL, v, 1);
-  if (lane == 31) ex = 0;
-  const int n = max(ex, cmax);
-  const int len = act ? plane_len<N>(W, n) : 0;
-  int sum = len;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_down_sync(FULL, sum, o);
-    if (lane + o < 32) sum += y;
-  }
-  n_out = n;
-  off_out = sum - len + csum;
-  cmax = max(cmax, __shfl_sync(FULL, v, 0));
-  csum += __shfl_sync(FULL, sum, 0);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const CompressParams P) {
-  using F = Fmt<T>;
-  using U = typename F::U;
-  using S = typename F::S;
-  constexpr int N = 64;
-  constexpr int Q = F::P - 2 - Geo<3>::G;  // quantisation bits (R6)
-  constexpr int C = Geo<3>::C;             // guard planes (R10)
-  constexpr int HDR = 2 + 3 + F::EBITS;    // mode, escalation, block exponent
-  constexpr int LEN_RAW = 2 + N * F::P;
-  constexpr int BUFW = chunk_buf_words3<T>();
-  constexpr bool WIDE = F::P == 64;
-  constexpr unsigned FULL = 0xffffffffu;
-
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* cbuf = reinterpret_cast<uint32_t*>(smem);
-  S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4);
-  uint64_t* s_pw = reinterpret_cast<uint64_t*>(bbuf + kChunk * 64);  // [warp][brick][plane] words
-  uint32_t* s_pi = reinterpret_cast<uint32_t*>(s_pw + kChunk * 64);  // [warp][brick][plane] off | n << 16
-  int* s_len = reinterpret_cast<int*>(s_pi + kChunk * 64);
-  int* s_off = s_len + 32;
-  int* s_mode = s_off + 32;
-  int* s_esc = s_mode + 32;
-  int* s_viol = s_esc + 32;
-  unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_viol + 32);
-  uint64_t* s_merr = reinterpret_cast<uint64_t*>(s_base + 2);
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int h = lane >> 4, t = lane & 15;
-  const unsigned HALF = h ? 0xffff0000u : 0x0000ffffu;
-  const int64_t chunk = blockIdx.x;
-  const int slot = warp * 2 + h;
-  const int64_t b = chunk * kChunk + slot;
-  const bool have = b < P.nbricks;
-
-  for (int w = tid; w < BUFW; w += kCompressThreads3) cbuf[w] = 0u;
-
-  int64_t bx = 0, by = 0, bz = 0;
-  if (have) {
-    bx = b % P.nb[0];
-    const int64_t r = b / P.nb[0];
-    by = r % P.nb[1];
-    bz = r / P.nb[1];
-  }
-  const int ly = t & 3, lz = t >> 2;
-  int nvx = 4, nvy = 4, nvz = 4;  // in-field extent of the brick per axis
-  if (have) {
-    nvx = (int)(P.dims[0] - 4 * bx < 4 ? P.dims[0] - 4 * bx : 4);
-    nvy = (int)(P.dims[1] - 4 * by < 4 ? P.dims[1] - 4 * by : 4);
-    nvz = (int)(P.dims[2] - 4 * bz < 4 ? P.dims[2] - 4 * bz : 4);
-  }
-  const bool line_in = have && ly < nvy && lz < nvz;
-  // R4: a lane outside the field takes the nearest in-field line's values
-  const int srcl = 16 * h + min(ly, nvy - 1) + 4 * min(lz, nvz - 1);
-  const bool partial = have && (nvx < 4 || nvy < 4 || nvz < 4);
-  const bool any_partial = __any_sync(FULL, partial);
-
-  T x[4], xt[4], e[4];
-  {
-    const T* field = reinterpret_cast<const T*>(P.field);
-    if (have) {
-      const int64_t gy = 4 * by + min(ly, nvy - 1), gz = 4 * bz + min(lz, nvz - 1);
-      const T* row = field + (gz * P.dims[1] + gy) * P.dims[0] + 4 * bx;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) x[m] = row[min(m, nvx - 1)];
-    } else {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) x[m] = T(0);
-    }
-  }
-  {
-    bool bad = false;
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-      if (line_in && m < nvx && not_finite<T>(x[m])) bad = true;
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(P.flags, kFlagNonFinite);
-  }
-  // Algorithm 1 starts from x~ = 0; the first residual is x - 0
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    xt[m] = T(0);
-    e[m] = F::sub(x[m], T(0));
-  }
-  S* buf = bbuf + warp * 128;
-  // buffer slots of this lane's line in each pass and of its coded coefficients
-  const int xx = t & 3, yq = t >> 2;
-  int ix[4], iy[4], iz[4], ir[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    ix[m] = sidx<T>(m, ly, lz, h);   // x-line of (y = ly, z = lz)
-    iy[m] = sidx<T>(xx, m, yq, h);   // y-line of (x = xx, z = yq)
-    iz[m] = sidx<T>(xx, yq, m, h);   // z-line of (x = xx, y = yq)
-    const int pos = kPerm3.pos[t + 16 * m];
-    ir[m] = sidx<T>(pos & 3, (pos >> 2) & 3, pos >> 4, h);
-  }
-  uint32_t tkeep[5];
-  transpose_masks(lane, tkeep);
-  unsigned long long pool_base = 0;  // thread 0 only
-  unsigned pool_nw = 0;
-
-  for (int i = 0; i < P.n; ++i) {  // one component per tau_i
-    const U tb = (U)P.tau_bits[i];
-    if (any_partial) {  // R4 padding of the residual
-      const T last = nvx == 1 ? e[0] : nvx == 2 ? e[1] : nvx == 3 ? e[2] : e[3];
-#pragma unroll
-      for (int m = 1; m < 4; ++m)
-        if (m >= nvx) e[m] = last;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) e[m] = __shfl_sync(FULL, e[m], srcl);
-    }
-    // R5: a brick whose residual meets tau_i on every in-field value is ZERO.
-    // (Every lane takes part in each vote: a vote behind && or || would be
-    // skipped by one half of the warp and leave the other half waiting.)
-    bool small = true;
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-      if (line_in && m < nvx && !within<T>(e[m], tb)) small = false;
-    const unsigned big_votes = __ballot_sync(FULL, !small);
-    const bool zero_blk = !have || ((big_votes & HALF) == 0u);
-    bool nf = false;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) nf |= not_finite<T>(e[m]);
-    const unsigned nf_votes = __ballot_sync(FULL, nf);
-    const bool raw_forced = !zero_blk && ((nf_votes & HALF) != 0u);
-
-    // R6: block exponent and exact quantisation
-    int be = 0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) be = max(be, biased_exp<T>(F::bits(e[m])));
-#pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) be = max(be, __shfl_xor_sync(FULL, be, o));
-    const int emax = block_emax_from_be<T>(be);
-    const int s = Q - emax;
-    S q[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) q[m] = quantize<T>(F::bits(e[m]), s);
-
-    // R7: lifting along x (in the lane), y and z (shared buffer)
-    lift_fwd(q[0], q[1], q[2], q[3]);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) buf[ix[m]] = q[m];
-    __syncwarp();
-    {
-      S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
-      lift_fwd(a, bq, c, d);
-      buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
-    }
-    __syncwarp();
-    {
-      S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
-      lift_fwd(a, bq, c, d);
-      buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
-    }
-    __syncwarp();
-    // R8, R9: coded order, negabinary.  Lane t holds coefficients t + 16j.
-    U u[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) u[j] = nb_fwd<T>(buf[ir[j]]);
-    __syncwarp();
-
-    // R10, R13: lowest coded plane; lowered until Eq. 1 holds in T
-    const int L = P.L[i];
-    int esc = 0, p = 0;
-    bool done = zero_blk || raw_forced, pass = false;
-    T xtc[4], ec[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      xtc[m] = xt[m];
-      ec[m] = e[m];
-    }
-    for (int round = 0; round < 8; ++round) {  // esc runs 0..7: at most 8 rounds
-      const bool active = !done;
-      const int pp = min(max(L + s - C - esc, 0), F::P);
-      const U keep = pp >= F::P ? U(0) : (U)~((U(1) << pp) - 1);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>((U)(u[j] & keep));
-      __syncwarp();
-      {
-        S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
-        lift_inv(a, bq, c, d);
-        buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
-      }
-      __syncwarp();
-      {
-        S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
-        lift_inv(a, bq, c, d);
-        buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
-      }
-      __syncwarp();
-      S r[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
-      __syncwarp();
-      lift_inv(r[0], r[1], r[2], r[3]);
-      bool ok = true;
-      T xtn[4], en[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const T xi = dequantize_val<T>(r[m], s);  // x_i = D(y_i)
-        xtn[m] = F::add(xt[m], xi);               // x~ + x_i (candidate)
-        en[m] = F::sub(x[m], xtn[m]);             // the next residual
-        if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
-      }
-      const bool pass_h = (__ballot_sync(FULL, !ok) & HALF) == 0u;
-      if (active) {
-        if (pass_h) {
-          pass = true;
-          done = true;
-          p = pp;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            xtc[m] = xtn[m];
-            ec[m] = en[m];
-          }
-        } else if (esc == 7 || pp == 0) {
-          done = true;
-        } else {
-          ++esc;
-        }
-      }
-      if (__all_sync(FULL, done)) break;
-    }
-
-    // R11: plane words by transposing the coefficient bits across the warp:
-    // lane l then holds plane l (and l + 32) of both bricks.
-    uint64_t WA0, WB0, WA1 = 0, WB1 = 0;
-    {
-      uint32_t tl[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) tl[j] = transpose32((uint32_t)u[j], lane, tkeep);
-      WA0 = (uint64_t)__byte_perm(tl[0], tl[1], 0x5410) | ((uint64_t)__byte_perm(tl[2], tl[3], 0x5410) << 32);
-      WB0 = (uint64_t)__byte_perm(tl[0], tl[1], 0x7632) | ((uint64_t)__byte_perm(tl[2], tl[3], 0x7632) << 32);
-      if constexpr (WIDE) {
-        uint32_t th[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) th[j] = transpose32((uint32_t)((uint64_t)u[j] >> 32), lane, tkeep);
-        WA1 = (uint64_t)__byte_perm(th[0], th[1], 0x5410) | ((uint64_t)__byte_perm(th[2], th[3], 0x5410) << 32);
-        WB1 = (uint64_t)__byte_perm(th[0], th[1], 0x7632) | ((uint64_t)__byte_perm(th[2], th[3], 0x7632) << 32);
-      }
-    }
-    const int pA = __shfl_sync(FULL, p, 0), pB = __shfl_sync(FULL, p, 16);
-    const bool passA = __shfl_sync(FULL, (int)pass, 0) != 0, passB = __shfl_sync(FULL, (int)pass, 16) != 0;
-    // planes P-1 .. p are coded, from the top: the high round (planes 32 + l)
-    // first for 64-bit coefficients, then planes l
-    int nA0 = 0, nA1 = 0, nB0 = 0, nB1 = 0, oA0 = 0, oA1 = 0, oB0 = 0, oB1 = 0;
-    int totA = 0, totB = 0;
-    {
-      int cmax = 0, csum = 0;
-      if constexpr (WIDE) plane_scan<N>(WA1, passA && lane + 32 >= pA, lane, cmax, csum, nA1, oA1);
-      plane_scan<N>(WA0, passA && lane >= pA, lane, cmax, csum, nA0, oA0);
-      totA = csum;
-    }
-    {
-      int cmax = 0, csum = 0;
-      if constexpr (WIDE) plane_scan<N>(WB1, passB && lane + 32 >= pB, lane, cmax, csum, nB1, oB1);
-      plane_scan<N>(WB0, passB && lane >= pB, lane, cmax, csum, nB0, oB0);
-      totB = csum;
-    }
-    const int lenC = HDR + (h ? totB : totA);
-    {  // plane p's word, code offset and significance count, for the coefficient lanes
-      uint64_t* pw = s_pw + warp * 128;
-      uint32_t* pi = s_pi + warp * 128;
-      pw[lane] = WA0;
-      pi[lane] = (uint32_t)oA0 | ((uint32_t)nA0 << 16);
-      pw[64 + lane] = WB0;
-      pi[64 + lane] = (uint32_t)oB0 | ((uint32_t)nB0 << 16);
-      if constexpr (WIDE) {
-        pw[32 + lane] = WA1;
-        pi[32 + lane] = (uint32_t)oA1 | ((uint32_t)nA1 << 16);
-        pw[96 + lane] = WB1;
-        pi[96 + lane] = (uint32_t)oB1 | ((uint32_t)nB1 << 16);
-      }
-    }
-
-    // R14: RAW replaces a longer CODED brick only if it also meets tau_i
-    bool raw_ok = false;
-    if (__any_sync(FULL, pass && lenC > LEN_RAW)) {
-      bool ok = true;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const T a = F::add(xt[m], e[m]);
-        if (line_in && m < nvx && !within<T>(F::sub(x[m], a), tb)) ok = false;
-      }
-      raw_ok = (__ballot_sync(FULL, !ok) & HALF) == 0u;
-    }
-    const int mode = zero_blk ? kModeZero : (pass && !(lenC > LEN_RAW && raw_ok)) ? kModeCoded : kModeRaw;
-    const int blen = !have ? 0 : mode == kModeZero ? 2 : mode == kModeRaw ? LEN_RAW : lenC;
-
-    // x~_i and the next residual, committed after the bits are written
-    // (a RAW brick stores the current residual)
-    T xtnew[4], enew[4];
-    int viol = 0;  // Eq. 1 failures left (only a RAW brick can have them)
-    U merr = 0;    // max |x - x~_i| over this lane's in-field values, as bits (Sec. 4.3)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      if (mode == kModeCoded) {
-        xtnew[m] = xtc[m];
-        enew[m] = ec[m];
-      } else if (mode == kModeRaw) {
-        xtnew[m] = F::add(xt[m], e[m]);
-        enew[m] = F::sub(x[m], xtnew[m]);
-      } else {
-        xtnew[m] = xt[m];
-        enew[m] = e[m];
-      }
-      if (line_in && m < nvx) {
-        if (!within<T>(enew[m], tb)) ++viol;
-        const U a = F::bits(enew[m]) & F::ABS;
-        merr = a > merr ? a : merr;
-      }
-    }
-#pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) {
-      viol += __shfl_xor_sync(FULL, viol, o);
-      const U y = (U)__shfl_xor_sync(FULL, (typename std::conditional<sizeof(U) == 8, unsigned long long, unsigned>::type)merr, o);
-      merr = y > merr ? y : merr;
-    }
-
-    if (t == 0) {
-      s_len[slot] = blen;
-      s_mode[slot] = have ? mode : -1;
-      s_esc[slot] = (have && mode == kModeCoded) ? esc : 0;
-      s_viol[slot] = have ? viol : 0;
-      s_merr[slot] = have ? (uint64_t)merr : 0ull;
-    }
-    __syncthreads();
-    if (warp == 0) {  // chunk layout: brick offsets, pool space, index entries
-      const int l0 = s_len[lane];
-      int incl = l0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-      }
-      s_off[lane] = incl - l0;
-      const int total = __shfl_sync(FULL, incl, 31);
-      const unsigned nw = (unsigned)((total + 63) >> 6);
-      const int md = s_mode[lane];
-      const unsigned cz = __popc(__ballot_sync(FULL, md == kModeZero));
-      const unsigned cc = __popc(__ballot_sync(FULL, md == kModeCoded));
-      const unsigned cr = __popc(__ballot_sync(FULL, md == kModeRaw));
-      int se = s_esc[lane], sv = s_viol[lane];
-      unsigned long long me = s_merr[lane];
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) {
-        se += __shfl_xor_sync(FULL, se, o);
-        sv += __shfl_xor_sync(FULL, sv, o);
-        const unsigned long long y = __shfl_xor_sync(FULL, me, o);
-        me = y > me ? y : me;
-      }
-      if (lane == 0) {
-        // pool space for the chunk; the atomic's result is first needed after
-        // this warp's share of the bit writes, which hides its latency
-        pool_base = nw ? atomicAdd(P.pool_used, (unsigned long long)nw) : 0ull;
-        pool_nw = nw;
-        const int64_t ci = (int64_t)i * P.nchunks + chunk;
-        P.chunk_nwords[ci] = nw;
-        uint32_t* cnt = P.chunk_counts + ci * 5;
-        cnt[0] = cz;
-        cnt[1] = cc;
-        cnt[2] = cr;
-        cnt[3] = (uint32_t)se;
-        cnt[4] = (uint32_t)sv;
-        if (P.chunk_maxerr) P.chunk_maxerr[ci] = me;
-      }
-      const int64_t bb = chunk * kChunk + lane;
-      if (bb < P.nbricks) {
-        P.brick_len[(int64_t)i * P.nbricks + bb] = (uint16_t)l0;
-        if (P.brick_off) P.brick_off[(int64_t)i * P.nbricks + bb] = (uint32_t)(incl - l0);
-      }
-    }
-    __syncthreads();
-    const int chunk_bits = s_off[31] + s_len[31];
-
-    // this component's bits of the warp's two bricks, into the chunk buffer
-    const uint32_t boff = (uint32_t)s_off[slot];
-    if (have && mode == kModeRaw) {
-      if (t == 0) or_bits(cbuf, boff, (uint64_t)kModeRaw);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) or_bits(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(e[m]));
-    } else if (have && mode == kModeCoded && t == 0) {
-      or_bits(cbuf, boff, (uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5));
-    }
-    const int modeA = __shfl_sync(FULL, mode, 0), modeB = __shfl_sync(FULL, mode, 16);
-    const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
-    // R11: each coded plane's verbatim bits, by the plane's owner lane ...
-    if (haveA && modeA == kModeCoded) {
-      const uint32_t base = (uint32_t)s_off[warp * 2] + HDR;
-      if (lane >= pA && nA0 > 0) or_bits(cbuf, base + oA0, WA0 & low_mask64(nA0));
-      if (WIDE && lane + 32 >= pA && nA1 > 0) or_bits(cbuf, base + oA1, WA1 & low_mask64(nA1));
-    }
-    if (haveB && modeB == kModeCoded) {
-      const uint32_t base = (uint32_t)s_off[warp * 2 + 1] + HDR;
-      if (lane >= pB && nB0 > 0) or_bits(cbuf, base + oB0, WB0 & low_mask64(nB0));
-      if (WIDE && lane + 32 >= pB && nB1 > 0) or_bits(cbuf, base + oB1, WB1 & low_mask64(nB1));
-    }
-    // ... and its group-test bits, one token per newly significant coefficient,
-    // by the lane that holds the coefficient
-    if (have && mode == kModeCoded && p < F::P) {
-      const uint64_t* pw = s_pw + warp * 128 + 64 * h;
-      const uint32_t* pi = s_pi + warp * 128 + 64 * h;
-      const uint32_t base = boff + HDR;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if ((u[j] >> p) == 0) continue;  // no bit at or above the lowest coded plane
-        const int pc = F::P - 1 - F::clz(u[j]);
-        const uint32_t info = pi[pc];
-        const int n = (int)(info >> 16), c = t + 16 * j;
-        if (c >= n) write_token(cbuf, base + (info & 0xffffu) + (uint32_t)n, pw[pc], n, c);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      xt[m] = xtnew[m];
-      e[m] = enew[m];
-    }
-    if (tid == 0) {
-      unsigned long long base = pool_base;
-      if (base + pool_nw > P.pool_words) {
-        atomicOr(P.flags, kFlagPoolOverflow);
-        base = ~0ull;
-      }
-      *s_base = base;
-      P.chunk_pool[(int64_t)i * P.nchunks + chunk] = base;
-    }
-    __syncthreads();
-    {  // append the chunk to the pool and clear the buffer for the next
-       // component (its first writes come after two more barriers)
-      const unsigned long long base = *s_base;
-      const int nw = (chunk_bits + 63) >> 6;
-      uint64_t* b64 = reinterpret_cast<uint64_t*>(cbuf);
-      for (int w = tid; w < nw; w += kCompressThreads3) {
-        if (base != ~0ull) P.pool[base + w] = b64[w];
-        b64[w] = 0ull;
-      }
-    }
-  }
+  compress3_chunk<T>(P, (int64_t)blockIdx.x, smem);
 }
 
 int compress_block_threads(int ndims) { return kCompressThreads3; }

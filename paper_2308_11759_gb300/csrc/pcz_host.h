@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -33,6 +34,7 @@ struct pc_streams {
   uint32_t* d_brick_off = nullptr;   // [n][nbricks] derived: first bit of each brick in its chunk
   pcz::CompDesc* d_desc = nullptr;   // [n]
   unsigned int* d_err = nullptr;
+  std::shared_ptr<void> backing;     // set when the device arrays live in arenas shared by a batch
 };
 
 namespace pcz {
@@ -48,5 +50,14 @@ pc_status check_box(const pc_streams* s, const pc_box* box, int64_t lo[3], int64
 // Retrieval job over a box (components k0+1..k into out); unit_begin = 0.
 BoxJob make_box_job(const pc_streams* s, int k0, int k, const int64_t lo[3], const int64_t hi[3], void* out);
 int64_t box_job_units(const BoxJob& J);
+// Exact double of a T bit pattern.
+double value_of_bits(uint64_t b, pc_dtype dt);
+// floor(log2 tau) and the bit pattern of the largest T not above tau.
+int floor_log2_of(double tau);
+uint64_t tau_bits_of(double tau, pc_dtype dt);
+bool tolerances_valid(const double* tau, int n);
+void field_geometry(int ndims, const int64_t* dims, int64_t d3[3], int64_t nb[3], int64_t* nbricks,
+                    int64_t* nchunks);
+bool device_pointer(const void* p);
 
 }  // namespace pcz

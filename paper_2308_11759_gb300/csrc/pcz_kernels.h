@@ -76,6 +76,40 @@ struct RetrieveParams {
 
 enum { kFlagNonFinite = 1u, kFlagPoolOverflow = 2u };
 
+// Batched construction: one persistent launch over the chunks of many
+// fields.  The work list is implicit: slot s (schedule order) covers field
+// slot_field[s], cut into items of slot_width[s] chunks (1 for a 3D field,
+// whose chunk the whole CTA codes; more for 1D/2D fields, one warp per
+// chunk); item g belongs to the slot s with slot_first[s] <= g <
+// slot_first[s + 1].
+struct BatchParams {
+  const CompressParams* fields;  // device array, one per field
+  const int32_t* slot_field;     // [nslots]
+  const int32_t* slot_width;     // [nslots]
+  const int32_t* slot_ndims;     // [nslots] dimensionality of the slot's field
+  const int64_t* slot_first;     // [nslots + 1]
+  int nslots;
+  int per_fetch;                 // items a CTA claims per atomic
+  int64_t nitems;
+  unsigned long long* next;      // work counter (zeroed before the launch)
+};
+
+// Segmented scan of chunk word counts: segment s is entries
+// [seg_start[s], seg_start[s] + seg_len[s]) of the chunk arrays.
+struct ScanParams {
+  const uint32_t* nwords;
+  uint64_t* word_off;
+  uint64_t* totals;              // [nseg]
+  const uint32_t* chunk_counts;  // [entries][5]
+  unsigned long long* counts;    // [nseg][5]
+  const uint64_t* chunk_maxerr;
+  unsigned long long* maxerr;    // [nseg]
+  const int64_t* seg_start;
+  const int64_t* seg_len;
+  int nseg;
+  int pad_;
+};
+
 // Launchers (each returns the launch error).
 cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaStream_t s);
 cudaError_t launch_retrieve(int dtype, int ndims, const RetrieveParams& p, cudaStream_t s);
@@ -89,6 +123,12 @@ cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint6
 cudaError_t launch_pack(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
                         const uint64_t* word_off, const uint64_t* comp_base, uint64_t* payload, int n,
                         int64_t nchunks, cudaStream_t s);
+cudaError_t launch_compress_batch(int dtype, const BatchParams* d_bp, int grid, cudaStream_t s);
+int compress_batch_grid(int dtype);  // persistent CTAs of the batched construction kernel
+cudaError_t launch_scan_segments(const ScanParams* d_sp, int nseg, cudaStream_t s);
+cudaError_t launch_pack_segments(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
+                                 const uint64_t* word_off, const int64_t* seg_start, const uint64_t* seg_base,
+                                 int nseg, int64_t nentries, uint64_t* payload, cudaStream_t s);
 cudaError_t launch_brick_offsets(const uint16_t* brick_len, uint32_t* brick_off, int n, int64_t nbricks,
                                  cudaStream_t s);
 cudaError_t launch_range(int dtype, const void* x, int64_t count, unsigned long long* enc, unsigned int* flags,

@@ -16,30 +16,23 @@ namespace pcz {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 
-// One CTA per component; tiles of 4096 chunks with a block-wide scan and a
-// running carry.
-__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __restrict__ nwords,
-                                                               uint64_t* __restrict__ word_off,
-                                                               uint64_t* __restrict__ totals,
-                                                               const uint32_t* __restrict__ chunk_counts,
-                                                               unsigned long long* __restrict__ counts,
-                                                               const uint64_t* __restrict__ chunk_maxerr,
-                                                               unsigned long long* __restrict__ maxerr,
-                                                               int64_t nchunks) {
+// One CTA per segment (a component's chunks); tiles of 4096 chunks with a
+// block-wide scan and a running carry.  in/out/cc/me point at the segment's
+// first chunk.
+__device__ __forceinline__ void scan_segment(const uint32_t* __restrict__ in, uint64_t* __restrict__ out,
+                                             const uint32_t* __restrict__ cc, const uint64_t* __restrict__ me,
+                                             int64_t nchunks, uint64_t* total_out,
+                                             unsigned long long* counts_out, unsigned long long* maxerr_out) {
   __shared__ uint64_t warp_sums[32];
   __shared__ uint64_t carry_s;
   __shared__ unsigned long long cnt_s[5];
   __shared__ unsigned long long merr_s;
-  const int comp = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t* in = nwords + (int64_t)comp * nchunks;
-  uint64_t* out = word_off + (int64_t)comp * nchunks;
-  const uint32_t* cc = chunk_counts + (int64_t)comp * nchunks * 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) carry_s = 0;
   if (tid < 5) cnt_s[tid] = 0;
   if (tid == 0) merr_s = 0;
   unsigned long long my_cnt[5] = {0, 0, 0, 0, 0};
   unsigned long long my_merr = 0;
-  const uint64_t* me = chunk_maxerr ? chunk_maxerr + (int64_t)comp * nchunks : nullptr;
   __syncthreads();
   for (int64_t tile = 0; tile < nchunks; tile += (int64_t)kScanThreads * kScanItems) {
     const int64_t first = tile + (int64_t)tid * kScanItems;
@@ -90,9 +83,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __
   for (int k = 0; k < 5; ++k) atomicAdd(&cnt_s[k], my_cnt[k]);
   atomicMax(&merr_s, my_merr);
   __syncthreads();
-  if (tid == 0) totals[comp] = carry_s;
-  if (tid == 0 && maxerr) maxerr[comp] = merr_s;
-  if (tid < 5) counts[comp * 5 + tid] = cnt_s[tid];
+  if (tid == 0) *total_out = carry_s;
+  if (tid < 5) counts_out[tid] = cnt_s[tid];
+  if (tid == 0 && maxerr_out) *maxerr_out = merr_s;
+}
+
+// Components of one field: segment c is chunks [c * nchunks, (c + 1) * nchunks).
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __restrict__ nwords,
+                                                               uint64_t* __restrict__ word_off,
+                                                               uint64_t* __restrict__ totals,
+                                                               const uint32_t* __restrict__ chunk_counts,
+                                                               unsigned long long* __restrict__ counts,
+                                                               const uint64_t* __restrict__ chunk_maxerr,
+                                                               unsigned long long* __restrict__ maxerr,
+                                                               int64_t nchunks) {
+  const int64_t c0 = (int64_t)blockIdx.x * nchunks;
+  scan_segment(nwords + c0, word_off + c0, chunk_counts + c0 * 5, chunk_maxerr ? chunk_maxerr + c0 : nullptr,
+               nchunks, totals + blockIdx.x, counts + 5 * blockIdx.x, maxerr ? maxerr + blockIdx.x : nullptr);
+}
+
+// Segments of a batch of fields, described in device memory (so that a
+// captured graph reads the current pointers).
+__global__ void __launch_bounds__(kScanThreads) k_scan_segments(const ScanParams* __restrict__ sp) {
+  const int seg = blockIdx.x;
+  if (seg >= sp->nseg) return;
+  const int64_t c0 = sp->seg_start[seg];
+  scan_segment(sp->nwords + c0, sp->word_off + c0, sp->chunk_counts + c0 * 5, sp->chunk_maxerr + c0,
+               sp->seg_len[seg], sp->totals + seg, sp->counts + 5 * seg, sp->maxerr + seg);
 }
 
 // One warp per (component, chunk): word-aligned copy from the pool.
@@ -191,6 +208,50 @@ cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint6
   if (n <= 0) return cudaSuccess;
   k_scan_chunks<<<n, kScanThreads, 0, s>>>(nwords, word_off, totals, chunk_counts, counts, chunk_maxerr, maxerr,
                                            nchunks);
+  return cudaGetLastError();
+}
+
+// One warp per chunk entry of a batch: its segment by binary search over the
+// segments' first entries, then a word-aligned copy to the segment's place.
+__global__ void __launch_bounds__(256) k_pack_segments(const uint64_t* __restrict__ pool,
+                                                       const uint32_t* __restrict__ nwords,
+                                                       const uint64_t* __restrict__ chunk_pool,
+                                                       const uint64_t* __restrict__ word_off,
+                                                       const int64_t* __restrict__ seg_start,
+                                                       const uint64_t* __restrict__ seg_base, int nseg,
+                                                       int64_t nentries, uint64_t* __restrict__ payload) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < nentries; wi += warps) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (seg_start[mid] <= wi)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const uint32_t nw = nwords[wi];
+    const uint64_t* src = pool + chunk_pool[wi];
+    uint64_t* dst = payload + seg_base[lo] + word_off[wi];
+    for (uint32_t w = lane; w < nw; w += 32) dst[w] = src[w];
+  }
+}
+
+cudaError_t launch_scan_segments(const ScanParams* d_sp, int nseg, cudaStream_t s) {
+  if (nseg <= 0) return cudaSuccess;
+  k_scan_segments<<<nseg, kScanThreads, 0, s>>>(d_sp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_segments(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
+                                 const uint64_t* word_off, const int64_t* seg_start, const uint64_t* seg_base,
+                                 int nseg, int64_t nentries, uint64_t* payload, cudaStream_t s) {
+  if (nentries == 0) return cudaSuccess;
+  int64_t blocks = (nentries + 7) / 8;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_pack_segments<<<(unsigned)blocks, 256, 0, s>>>(pool, nwords, chunk_pool, word_off, seg_start, seg_base, nseg,
+                                                   nentries, payload);
   return cudaGetLastError();
 }
 

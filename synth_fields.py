@@ -26,11 +26,17 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def gaussians(shape, n_gauss: int = 32, seed: int = 1, dtype=np.float64, noise: float = 1e-3):
-    """Sum of n_gauss random anisotropic Gaussians plus white noise."""
+def gaussians(shape, n_gauss: int = 32, seed: int = 1, dtype=np.float64, noise: float = 1e-3, device=None):
+    """Sum of n_gauss random anisotropic Gaussians plus white noise.
+
+    device=None builds it with numpy and returns a numpy array; device="cuda"
+    builds it with torch there (same Gaussians; the noise comes from torch's
+    generator seeded with `seed`) and returns a torch tensor."""
     rng = _rng(seed)
     shape = tuple(int(s) for s in shape)
     nd = len(shape)
+    if device is not None:
+        return _gaussians_torch(shape, n_gauss, seed, rng, dtype, noise, device)
     axes = [np.arange(s, dtype=np.float64) for s in shape]
     out = np.zeros(shape, dtype=np.float64)
     for _ in range(n_gauss):
@@ -48,6 +54,31 @@ def gaussians(shape, n_gauss: int = 32, seed: int = 1, dtype=np.float64, noise: 
     if noise:
         out += rng.normal(0.0, noise, size=shape)
     return out.astype(dtype)
+
+
+def _gaussians_torch(shape, n_gauss, seed, rng, dtype, noise, device):
+    import torch
+
+    nd = len(shape)
+    axes = [torch.arange(s, device=device, dtype=torch.float64) for s in shape]
+    out = torch.zeros(shape, device=device, dtype=torch.float64)
+    for _ in range(n_gauss):
+        centre = [rng.uniform(0, s) for s in shape]
+        sigma = [rng.uniform(2.0, 16.0) for _ in shape]
+        amp = rng.uniform(-1.0, 1.0)
+        g = None
+        for a in range(nd):
+            prof = torch.exp(-0.5 * ((axes[a] - centre[a]) / sigma[a]) ** 2)
+            view = [1] * nd
+            view[a] = shape[a]
+            prof = prof.reshape(view)
+            g = prof if g is None else g * prof
+        out += amp * g
+    if noise:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed))
+        out += noise * torch.randn(shape, generator=gen, device=device, dtype=torch.float64)
+    return out.to(torch.float32 if np.dtype(dtype) == np.float32 else torch.float64)
 
 
 def _powerlaw_numpy(shape, rng):
