@@ -38,18 +38,24 @@ __constant__ PermTable kPerm3r = make_perm(64);
 
 constexpr int kRWarps = 8;
 constexpr int kRThreads = 32 * kRWarps;
-constexpr int kRound = 8;  // components per round: one per warp while parsing
-constexpr int kSlot = 24;  // plane words per block kept in shared memory
+constexpr int kRound = 8;    // components per round
+constexpr int kTasks = 512;  // parse tasks (block of one brick and component) per round
+constexpr int kSlot = 15;    // plane words per block kept in shared memory (3 CTAs per SM fit)
 
 struct BlockMeta {
   uint64_t off;  // first bit of the brick in the component's payload
-  int mode, s, p, top;
+  int16_t s;     // scale exponent (R6), within [-1100, 1100]
+  int8_t p;      // lowest coded plane, 0..64
+  int8_t top;    // highest non-empty plane, -1 if none
+  int8_t mode;
+  int8_t pad_[3];
 };
+static_assert(sizeof(BlockMeta) == 16, "block header size");
 
 template <typename T>
 __host__ __device__ constexpr size_t retrieve_smem3() {
-  return (size_t)kRound * 32 * kSlot * sizeof(uint64_t)  // plane slots
-         + (size_t)kRound * 32 * sizeof(BlockMeta)       // block headers
+  return (size_t)kTasks * kSlot * sizeof(uint64_t)  // plane slots
+         + (size_t)kTasks * sizeof(BlockMeta)       // block headers
          + (size_t)kRWarps * 128 * sizeof(typename Fmt<T>::S);  // brick buffers
 }
 
@@ -60,7 +66,7 @@ __host__ __device__ constexpr int spill_per_block() {  // planes below a block's
 
 template <typename T>
 __host__ __device__ constexpr size_t spill_words_per_cta() {
-  return (size_t)kRound * 32 * spill_per_block<T>();
+  return (size_t)kTasks * spill_per_block<T>();
 }
 
 // R11 decoding of planes P-1 .. p of one block, starting at bit pos and ending
@@ -248,12 +254,12 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
   }
 }
 
-// Parse phase: thread L decodes component base + L / ub of unit brick
-// L % ub (ub = bricks per unit) into slot L.  Components a brick takes from
-// the cache are not parsed (ZERO).
+// Parse task L decodes component base + L / ub of unit brick L % ub (ub =
+// bricks per unit) into slot L.  Components a brick takes from the cache
+// are not parsed (ZERO).
 template <typename T>
 __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, int64_t unit0, int ub, int base,
-                                           int nc, uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
+                                           int nc, int L, uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
   using F = Fmt<T>;
   constexpr int N = 64;
   constexpr int Q = F::P - 2 - Geo<3>::G;
@@ -261,7 +267,6 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
   constexpr int HDR = 2 + 3 + F::EBITS;
   constexpr int EMAXT = (1 << (F::EXPW - 1));  // frexp exponent of the largest finite T
   constexpr int SP = spill_per_block<T>();
-  const int L = threadIdx.x;
   const int jj = L / ub;
   const int64_t g = unit0 + L % ub;
   if (jj >= nc || g >= J.nbox) return;
@@ -272,7 +277,8 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
     BlockMeta bm;
     bm.off = 0;
     bm.mode = kModeZero;
-    bm.s = bm.p = 0;
+    bm.s = 0;
+    bm.p = 0;
     bm.top = -1;
     meta[L] = bm;
     return;
@@ -307,24 +313,44 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
   }
   BlockMeta bm;
   bm.off = off;
-  bm.mode = mode;
-  bm.s = s;
-  bm.p = p;
-  bm.top = top;
+  bm.mode = (int8_t)mode;
+  bm.s = (int16_t)s;
+  bm.p = (int8_t)p;
+  bm.top = (int8_t)top;
   meta[L] = bm;
 }
 
+// Parse phase with warp-granular work stealing: each warp takes the next 32
+// tasks (32 bricks of one component, so the lanes' blocks are alike) until
+// the round's tasks are gone.  Tasks are ordered component-major, the first
+// and costliest component first, so no warp waits at the barrier behind a
+// fixed share of long blocks.
 template <typename T>
-__global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R) {
+__device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, int64_t unit0, int ub, int base,
+                                            int nc, int* next, uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
+  const int lane = threadIdx.x & 31;
+  const int ntask = nc * ub;
+  for (;;) {
+    int t0 = 0;
+    if (lane == 0) t0 = atomicAdd(next, 32);
+    t0 = __shfl_sync(0xffffffffu, t0, 0);
+    if (t0 >= ntask) break;
+    if (t0 + lane < ntask) parse_task<T>(J, err, unit0, ub, base, nc, t0 + lane, slots, meta, spill);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRThreads, sizeof(T) == 4 ? 3 : 2) k_retrieve3(const RetrieveParams R) {
   using F = Fmt<T>;
   using S = typename F::S;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int SP = spill_per_block<T>();
 
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* slots = reinterpret_cast<uint64_t*>(smem);                          // [256][kSlot]
-  BlockMeta* meta = reinterpret_cast<BlockMeta*>(slots + kRound * 32 * kSlot);  // [256]
-  S* bufs = reinterpret_cast<S*>(meta + kRound * 32);                           // [kRWarps][128]
+  uint64_t* slots = reinterpret_cast<uint64_t*>(smem);                // [kTasks][kSlot]
+  BlockMeta* meta = reinterpret_cast<BlockMeta*>(slots + kTasks * kSlot);  // [kTasks]
+  S* bufs = reinterpret_cast<S*>(meta + kTasks);                           // [kRWarps][128]
+  __shared__ int s_next;  // next parse task of the round
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, t = lane & 15;
   S* buf = bufs + warp * 128;
   uint64_t* spill = R.spill + (size_t)blockIdx.x * spill_words_per_cta<T>();
@@ -361,6 +387,7 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
       }
       reinterpret_cast<uint64_t*>(&sJ)[threadIdx.x] = reinterpret_cast<const uint64_t*>(R.jobs + lo)[threadIdx.x];
     }
+    if (threadIdx.x == kRThreads - 1) s_next = 0;
     __syncthreads();
     T* out = reinterpret_cast<T*>(J.out);
     const int umult = J.umult;
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
       // one round: every warp parses, then each warp rebuilds its umult
       // brick pairs and writes them out
       const int nc = J.k - J.k0;
-      parse_task<T>(J, R.err, unit0, ub, J.k0, nc, slots, meta, spill);
+      parse_round<T>(J, R.err, unit0, ub, J.k0, nc, &s_next, slots, meta, spill);
       __syncthreads();
       for (int q = 0; q < umult; ++q) {
         const int uA = 2 * (umult * warp + q);  // unit-local index of the pair's first brick
@@ -382,7 +409,8 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
         for (int jj = 0; jj < nc; ++jj) {  // Algorithm 2, components in ascending order
           BlockMeta mA, mB;
           mA.mode = mB.mode = kModeZero;
-          mA.s = mB.s = mA.p = mB.p = 0;
+          mA.s = mB.s = 0;
+          mA.p = mB.p = 0;
           mA.top = mB.top = -1;
           mA.off = mB.off = 0;
           const int L = jj * ub + uA;
@@ -412,7 +440,7 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
       }
       for (int base = J.k0; base < J.k; base += kRound) {
         const int nc = min(kRound, J.k - base);
-        parse_task<T>(J, R.err, unit0, 32, base, nc, slots, meta, spill);
+        parse_round<T>(J, R.err, unit0, 32, base, nc, &s_next, slots, meta, spill);
         __syncthreads();
         for (int jj = 0; jj < nc; ++jj) {
 #pragma unroll
@@ -422,7 +450,8 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
             const bool haveB = __shfl_sync(FULL, (int)BL[q].have, 16) != 0;
             BlockMeta mA, mB;
             mA.mode = mB.mode = kModeZero;
-            mA.s = mB.s = mA.p = mB.p = 0;
+            mA.s = mB.s = 0;
+          mA.p = mB.p = 0;
             mA.top = mB.top = -1;
             mA.off = mB.off = 0;
             const int L = jj * 32 + uA;
@@ -435,7 +464,9 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
             for (int m = 0; m < 4; ++m) xt[q][m] = F::add(xt[q][m], xi[m]);
           }
         }
-        __syncthreads();  // the next round's parse reuses the slots
+        __syncthreads();  // the next round's parse reuses the slots and the task counter
+        if (threadIdx.x == 0) s_next = 0;
+        __syncthreads();
       }
       if (R.write) {
 #pragma unroll
@@ -451,11 +482,11 @@ __global__ void __launch_bounds__(kRThreads) k_retrieve3(const RetrieveParams R)
 int retrieve_block_threads(int ndims) { return kRThreads; }
 
 // Brick pairs per warp in a unit (a unit is 16 * umult bricks): as many as
-// keep one round's parse tasks (bricks x components) within the CTA's 256
-// threads; several rounds use 2 pairs per warp.
+// keep one round's parse tasks (bricks x components) within kTasks, two per
+// thread, so that warps can steal work; several rounds use 2 pairs per warp.
 int retrieve_unit_mult(int ncomp) {
   if (ncomp <= 0 || ncomp > kRound) return 2;
-  const int m = 16 / ncomp;
+  const int m = (kTasks / 16) / ncomp;
   return m < 1 ? 1 : m;
 }
 
