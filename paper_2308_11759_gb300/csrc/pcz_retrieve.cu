@@ -69,41 +69,110 @@ __host__ __device__ constexpr size_t spill_words_per_cta() {
   return (size_t)kTasks * spill_per_block<T>();
 }
 
+// Group-test part of one plane (R11), token by token: a test bit, and on 1
+// the run of coefficient bits up to and including the next 1.  W receives
+// the new coefficients' bits; n and pos advance.  Returns false when a test
+// bit promises a 1 that the run does not hold.
+__device__ __forceinline__ bool parse_tokens_serial(BitReader& br, uint64_t& pos, int& n, uint64_t& W) {
+  constexpr int N = 64;
+  for (int it = 0; it < N && n < N; ++it) {
+    const uint64_t v = br.peek(pos);
+    if (!(v & 1ull)) {  // test 0: nothing more in this plane
+      pos += 1;
+      return true;
+    }
+    const uint64_t rest = v >> 1;
+    int tz;
+    if (rest) {
+      tz = __ffsll((long long)rest) - 1;
+    } else {
+      if (!(br.peek(pos + 64) & 1ull)) return false;
+      tz = 63;
+    }
+    if (n + tz >= N) return false;
+    W |= 1ull << (n + tz);
+    n += tz + 1;
+    pos += (uint64_t)tz + 2;
+  }
+  return true;
+}
+
+// The same from one 64-bit window g of the stream.  Inside a plane's group
+// part the 1 bits alternate between test bits and run terminators (a test 1
+// is always followed by its run, a run always ends in a 1, and the next test
+// bit follows the terminator at once), so the terminators are the 1 bits of
+// even rank: g & ~prefix_xor(g).  Terminator k (1-based) at bit t marks
+// coefficient n + t - k.  The part ends after the terminator that is not
+// followed by a test 1, or that makes coefficient N - 1 significant.  When the
+// part runs past the window the serial decoder takes over at the next token.
+__device__ __forceinline__ bool parse_tokens(BitReader& br, uint64_t& pos, int& n, uint64_t& W) {
+  constexpr int N = 64;
+  const uint64_t g = br.peek(pos);
+  if (!(g & 1ull)) {
+    pos += 1;
+    return true;
+  }
+  uint64_t m = g;
+  m ^= m << 1;
+  m ^= m << 2;
+  m ^= m << 4;
+  m ^= m << 8;
+  m ^= m << 16;
+  m ^= m << 32;
+  uint64_t term = g & ~m;
+  const int n0 = n;
+  int k = 0, next = 0;  // tokens decoded; window bit of the next test bit
+  while (term) {
+    const int t = __ffsll((long long)term) - 1;
+    term &= term - 1;
+    ++k;
+    const int c = n0 + t - k;
+    if (c >= N) return false;
+    W |= 1ull << c;
+    n = c + 1;
+    next = t + 1;
+    if (c == N - 1) {  // every coefficient significant: no closing test bit
+      pos += (uint64_t)next;
+      return true;
+    }
+    if (t == 63) break;             // the follower lies beyond the window
+    if (!((g >> (t + 1)) & 1ull)) {  // closing test 0
+      pos += (uint64_t)next + 1;
+      return true;
+    }
+  }
+  pos += (uint64_t)next;
+  return parse_tokens_serial(br, pos, n, W);
+}
+
 // R11 decoding of planes P-1 .. p of one block, starting at bit pos and ending
 // exactly at end.  Plane pl (for pl in [p, top], top = the highest non-empty
 // plane, -1 if none) goes to slot[top - pl], or to spill[top - pl - kSlot]
-// below the slot.  Returns false on a malformed block; every loop is bounded.
+// below the slot.  Planes above the first significant coefficient are one 0
+// test bit each and are skipped together.  Returns false on a malformed
+// block; every loop is bounded.
 template <typename T>
 __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, uint64_t* slot, uint64_t* spill,
                              int& top) {
   constexpr int N = 64;
   int n = 0;
   top = -1;
-  for (int pl = Fmt<T>::P - 1; pl >= p; --pl) {
+  int pl = Fmt<T>::P - 1;
+  while (pl >= p) {
+    const uint64_t v = br.peek(pos);
+    if (v & 1ull) break;
+    const int z = v ? __ffsll((long long)v) - 1 : 64;
+    const int skip = min(z, pl - p + 1);
+    pos += (uint64_t)skip;
+    pl -= skip;
+  }
+  for (; pl >= p; --pl) {
     uint64_t W = 0;
     if (n > 0) {
       W = br.peek(pos) & low_mask64(n);
       pos += (uint64_t)n;
     }
-    for (int it = 0; it < N && n < N; ++it) {
-      const uint64_t v = br.peek(pos);
-      if (!(v & 1ull)) {  // test 0: nothing more in this plane
-        pos += 1;
-        break;
-      }
-      const uint64_t rest = v >> 1;
-      int tz;
-      if (rest) {
-        tz = __ffsll((long long)rest) - 1;
-      } else {
-        if (!(br.peek(pos + 64) & 1ull)) return false;
-        tz = 63;
-      }
-      if (n + tz >= N) return false;  // a promised 1 that never came
-      W |= 1ull << (n + tz);
-      n += tz + 1;
-      pos += (uint64_t)tz + 2;
-    }
+    if (n < N && !parse_tokens(br, pos, n, W)) return false;
     if (pos > end) return false;
     if (W && top < 0) top = pl;
     if (top >= 0) {
