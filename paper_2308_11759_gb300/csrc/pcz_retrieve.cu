@@ -40,7 +40,11 @@ constexpr int kRWarps = 8;
 constexpr int kRThreads = 32 * kRWarps;
 constexpr int kRound = 8;    // components per round
 constexpr int kTasks = 512;  // parse tasks (block of one brick and component) per round
-constexpr int kSlot = 15;    // plane words per block kept in shared memory (3 CTAs per SM fit)
+// plane words per block kept in shared memory: as many as let 3 CTAs share an SM
+template <typename T>
+struct Slots {
+  static constexpr int n = sizeof(T) == 4 ? 15 : 14;
+};
 
 struct BlockMeta {
   uint64_t off;  // first bit of the brick in the component's payload
@@ -54,14 +58,14 @@ static_assert(sizeof(BlockMeta) == 16, "block header size");
 
 template <typename T>
 __host__ __device__ constexpr size_t retrieve_smem3() {
-  return (size_t)kTasks * kSlot * sizeof(uint64_t)  // plane slots
+  return (size_t)kTasks * Slots<T>::n * sizeof(uint64_t)  // plane slots
          + (size_t)kTasks * sizeof(BlockMeta)       // block headers
          + (size_t)kRWarps * 128 * sizeof(typename Fmt<T>::S);  // brick buffers
 }
 
 template <typename T>
 __host__ __device__ constexpr int spill_per_block() {  // planes below a block's slot
-  return Fmt<T>::P - kSlot;
+  return Fmt<T>::P - Slots<T>::n;
 }
 
 template <typename T>
@@ -147,7 +151,7 @@ __device__ __forceinline__ bool parse_tokens(BitReader& br, uint64_t& pos, int& 
 
 // R11 decoding of planes P-1 .. p of one block, starting at bit pos and ending
 // exactly at end.  Plane pl (for pl in [p, top], top = the highest non-empty
-// plane, -1 if none) goes to slot[top - pl], or to spill[top - pl - kSlot]
+// plane, -1 if none) goes to slot[top - pl], or to spill[top - pl - Slots<T>::n]
 // below the slot.  Planes above the first significant coefficient are one 0
 // test bit each and are skipped together.  Returns false on a malformed
 // block; every loop is bounded.
@@ -177,10 +181,10 @@ __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, u
     if (W && top < 0) top = pl;
     if (top >= 0) {
       const int rel = top - pl;
-      if (rel < kSlot)
+      if (rel < Slots<T>::n)
         slot[rel] = W;
       else
-        spill[rel - kSlot] = W;
+        spill[rel - Slots<T>::n] = W;
     }
   }
   return pos == end;
@@ -268,7 +272,7 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
     auto fetch = [&](const BlockMeta& mX, bool cX, const uint64_t* sX, const uint64_t* pX, int pl) {
       if (!cX || pl < mX.p || pl > mX.top) return (uint64_t)0;
       const int rel = mX.top - pl;
-      return rel < kSlot ? sX[rel] : pX[rel - kSlot];
+      return rel < Slots<T>::n ? sX[rel] : pX[rel - Slots<T>::n];
     };
     const uint64_t WA0 = fetch(mA, cA, sA, pA, lane), WB0 = fetch(mB, cB, sB, pB, lane);
     U u[4];
@@ -371,7 +375,7 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
     if (ok) {
       s = Q - emax;
       p = min(max(cd.L + s - C - esc, 0), F::P);
-      ok = parse_planes<T>(br, off + HDR, end, p, slots + L * kSlot, spill + L * SP, top);
+      ok = parse_planes<T>(br, off + HDR, end, p, slots + L * Slots<T>::n, spill + L * SP, top);
     }
   } else {
     ok = false;
@@ -409,15 +413,15 @@ __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRThreads, sizeof(T) == 4 ? 3 : 2) k_retrieve3(const RetrieveParams R) {
+__global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams R) {
   using F = Fmt<T>;
   using S = typename F::S;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int SP = spill_per_block<T>();
 
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* slots = reinterpret_cast<uint64_t*>(smem);                // [kTasks][kSlot]
-  BlockMeta* meta = reinterpret_cast<BlockMeta*>(slots + kTasks * kSlot);  // [kTasks]
+  uint64_t* slots = reinterpret_cast<uint64_t*>(smem);                // [kTasks][Slots<T>::n]
+  BlockMeta* meta = reinterpret_cast<BlockMeta*>(slots + kTasks * Slots<T>::n);  // [kTasks]
   S* bufs = reinterpret_cast<S*>(meta + kTasks);                           // [kRWarps][128]
   __shared__ int s_next;  // next parse task of the round
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, t = lane & 15;
@@ -486,7 +490,7 @@ __global__ void __launch_bounds__(kRThreads, sizeof(T) == 4 ? 3 : 2) k_retrieve3
           if (haveA) mA = meta[L];
           if (haveB) mB = meta[L + 1];
           T xi[4];
-          rebuild_pair<T>(mA, mB, slots + L * kSlot, slots + (L + 1) * kSlot, spill + L * SP, spill + (L + 1) * SP,
+          rebuild_pair<T>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP, spill + (L + 1) * SP,
                           &J.comp[J.k0 + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
           for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // x~ += x_j
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(kRThreads, sizeof(T) == 4 ? 3 : 2) k_retrieve3
             if (haveA) mA = meta[L];
             if (haveB) mB = meta[L + 1];
             T xi[4];
-            rebuild_pair<T>(mA, mB, slots + L * kSlot, slots + (L + 1) * kSlot, spill + L * SP,
+            rebuild_pair<T>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP,
                             spill + (L + 1) * SP, &J.comp[base + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
             for (int m = 0; m < 4; ++m) xt[q][m] = F::add(xt[q][m], xi[m]);
