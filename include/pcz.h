@@ -16,8 +16,11 @@
  *  - Fields are dense, x fastest: element (ix, iy, iz) sits at
  *    ix + dims[0] * (iy + dims[1] * iz).  ndims is 1, 2 or 3; extents need not
  *    be multiples of 4.
- *  - Device pointers are CUDA global memory on the current device; host
- *    pointers are accepted where stated and are copied through the same stream.
+ *  - Device pointers are CUDA global memory on the current device.  Host
+ *    pointers are accepted where stated: pinned (page-locked) host memory is
+ *    read or written in place by the kernels through its device mapping (on
+ *    a Grace-Blackwell node over the C2C link, overlapped with the
+ *    computation); pageable host memory is copied through the same stream.
  *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
  *    are asynchronous on it except where they must read a result back.
  *  - The caller owns its input and output buffers.  The library owns the
@@ -172,9 +175,10 @@ pc_status pc_stream_read(const pc_streams *s, int i, uint64_t word_off, uint64_t
 void pc_streams_free(pc_streams *s);
 
 /*
- * The range min/max of a device field (Sec. 5.1: tau_0 is the range of the
- * field values), reduced on cuda_stream; *vmin and *vmax receive the extreme
- * values as doubles.  Synchronises.  PC_ERR_NONFINITE if a value is not finite.
+ * The range min/max of a field in device or pinned host memory (Sec. 5.1:
+ * tau_0 is the range of the field values), reduced on cuda_stream; *vmin and
+ * *vmax receive the extreme values as doubles.  Synchronises.
+ * PC_ERR_NONFINITE if a value is not finite; PC_ERR_ARG for pageable memory.
  */
 pc_status pc_field_range(const void *d_field, int64_t count, pc_dtype dtype, void *cuda_stream, double *vmin,
                          double *vmax);

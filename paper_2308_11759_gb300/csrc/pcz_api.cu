@@ -81,6 +81,29 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Address under which the kernels can use caller memory directly: device or
+// managed memory as is, pinned host memory through its device mapping (on a
+// Grace-Blackwell node the kernels then read and write it over the C2C link,
+// so the transfer overlaps the computation).  False for pageable memory.
+bool kernel_pointer(const void* p, const void** dptr, bool* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *host = false;
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    *dptr = p;
+    return true;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *dptr = a.devicePointer;
+    *host = true;
+    return true;
+  }
+  return false;
+}
+
 // floor(log2 tau) from the bit pattern of a positive finite double.
 int floor_log2_bits(double tau) {
   uint64_t b;
@@ -349,7 +372,8 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
   if (e == cudaSuccess) e = scr.get((void**)&(ptr), (size_t)(bytes));
     const void* d_field = field;
     void* staged = nullptr;
-    if (!is_device_ptr(field)) {  // host field: copy it in on the stream
+    bool mapped_host = false;
+    if (!kernel_pointer(field, &d_field, &mapped_host)) {  // pageable host field: copy it in on the stream
       SCR(staged, count * dsize(dtype));
       if (e == cudaSuccess) e = cudaMemcpyAsync(staged, field, count * dsize(dtype), cudaMemcpyHostToDevice, st);
       d_field = staged;
@@ -512,7 +536,13 @@ static pc_status retrieve_common(const pc_streams* s, int k0, int k, const pc_bo
   pc_status r = box_of(s, box, lo, hi);
   if (r != PC_OK) return r;
   const size_t bytes = (size_t)((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])) * dsize(s->dtype);
-  if (is_device_ptr(buf)) return run_retrieve(s, k0, k, lo, hi, buf, 1, st);
+  const void* kp = nullptr;
+  bool host = false;
+  if (kernel_pointer(buf, &kp, &host)) {  // device memory, or pinned host memory written in place
+    r = run_retrieve(s, k0, k, lo, hi, const_cast<void*>(kp), 1, st);
+    if (r == PC_OK && host) CK(cudaStreamSynchronize(st));
+    return r;
+  }
   Scratch scr(st);
   void* d = nullptr;
   CK(scr.get(&d, bytes));
@@ -835,7 +865,10 @@ pc_status pc_field_range(const void* d_field, int64_t count, pc_dtype dtype, voi
   g_err.clear();
   if (!d_field || count < 1 || !vmin || !vmax) return fail(PC_ERR_ARG, "bad arguments");
   if (dtype != PC_F32 && dtype != PC_F64) return fail(PC_ERR_ARG, "bad dtype");
-  if (!is_device_ptr(d_field)) return fail(PC_ERR_ARG, "field must be device memory");
+  const void* kp = nullptr;
+  bool host = false;
+  if (!kernel_pointer(d_field, &kp, &host)) return fail(PC_ERR_ARG, "field must be device or pinned host memory");
+  d_field = kp;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Scratch scr(st);
   unsigned long long* enc = nullptr;

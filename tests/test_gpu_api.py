@@ -141,6 +141,18 @@ def test_host_buffers(P):
     part = np.empty((5, 6, 7), dtype=np.float32)
     host.retrieve(k=4, box=([3, 2, 1], [8, 8, 8]), out=part)
     assert np.array_equal(part, dev.retrieve(k=4).cpu().numpy()[3:8, 2:8, 1:8])
+    # pinned host memory: read and written in place by the kernels
+    xp = torch.from_numpy(x).pin_memory()
+    pinned = P.compress(xp, tau)
+    assert pinned.serialize() == dev.serialize()
+    assert P.field_range(xp) == P.field_range(torch.from_numpy(x).cuda())
+    op = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+    pinned.retrieve(k=3, out=op)
+    assert torch.equal(op.view(torch.uint8), dev.retrieve(k=3).cpu().view(torch.uint8))
+    acc = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+    pinned.retrieve(k=2, out=acc)
+    pinned.refine(2, 5, acc)  # x~_2 read from and x~_5 written to pinned memory
+    assert torch.equal(acc.view(torch.uint8), dev.retrieve(k=5).cpu().view(torch.uint8))
 
 
 def test_error_statuses(P):
