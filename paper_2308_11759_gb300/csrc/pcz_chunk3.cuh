@@ -151,8 +151,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     if (have) {
       const int64_t gy = 4 * by + min(ly, nvy - 1), gz = 4 * bz + min(lz, nvz - 1);
       const T* row = field + (gz * P.dims[1] + gy) * P.dims[0] + 4 * bx;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) x[m] = row[min(m, nvx - 1)];
+      load_line<T>(row, nvx, x);
     } else {
 #pragma unroll
       for (int m = 0; m < 4; ++m) x[m] = T(0);

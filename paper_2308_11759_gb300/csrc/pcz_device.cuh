@@ -332,6 +332,51 @@ __device__ __forceinline__ int sidx(int x, int y, int z, int h) {
     return 32 * z + 16 * h + 4 * ((y + z) & 3) + ((x + z) & 3);
 }
 
+// One x-line of a brick (4 consecutive values) between registers and memory:
+// a single 16-byte access per 16 bytes when the line is whole and aligned
+// (fewer transactions, which matters most when the memory is on the host side
+// of the C2C link), element by element otherwise.
+template <typename T>
+__device__ __forceinline__ void store_line(T* dst, const T* v, const bool* ok) {
+  if (ok[0] && ok[1] && ok[2] && ok[3] && ((uintptr_t)dst & 15) == 0) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      reinterpret_cast<double2*>(dst)[0] = make_double2(v[0], v[1]);
+      reinterpret_cast<double2*>(dst)[1] = make_double2(v[2], v[3]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    if (ok[m]) dst[m] = v[m];
+}
+
+// Loads the line's first nv (1..4) values; lanes past them repeat the last
+// (R4 edge replication along x).
+template <typename T>
+__device__ __forceinline__ void load_line(const T* src, int nv, T* v) {
+  if (nv == 4 && ((uintptr_t)src & 15) == 0) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(src);
+      v[0] = a.x;
+      v[1] = a.y;
+      v[2] = a.z;
+      v[3] = a.w;
+    } else {
+      const double2 a = reinterpret_cast<const double2*>(src)[0];
+      const double2 b = reinterpret_cast<const double2*>(src)[1];
+      v[0] = a.x;
+      v[1] = a.y;
+      v[2] = b.x;
+      v[3] = b.y;
+    }
+    return;
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) v[m] = src[min(m, nv - 1)];
+}
+
 // Sequential bit reader over a word stream with the two current words in
 // registers: one load per 64 bits consumed.  Positions must not decrease.
 struct BitReader {

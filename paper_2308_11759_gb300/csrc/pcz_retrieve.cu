@@ -496,9 +496,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
           for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // x~ += x_j
         }
         if (R.write) {
-#pragma unroll
-          for (int m = 0; m < 4; ++m)
-            if (BL.vm[m]) out[BL.orow + m] = xt[m];
+          store_line<T>(out + BL.orow, xt, BL.vm);
         }
       }
     } else {
@@ -544,9 +542,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       if (R.write) {
 #pragma unroll
         for (int q = 0; q < 2; ++q)
-#pragma unroll
-          for (int m = 0; m < 4; ++m)
-            if (BL[q].vm[m]) out[BL[q].orow + m] = xt[q][m];
+          store_line<T>(out + BL[q].orow, xt[q], BL[q].vm);
       }
     }
   }
