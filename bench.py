@@ -49,6 +49,11 @@ sys.path.insert(0, ROOT)
 
 N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
+# DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
+# capture of the current kernels (profiles/retrieve3_compress3_320cube_sections.md).
+TRAFFIC = {"retrieve": 1144261771}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 16 retrieval launches of "
+                  "the 320^3 case, scaled by the bricks processed to 512^3")
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
                   "384x384x256 (not multiples of 4), half sums of Gaussians and half k^-5/3 spectra, 6 components "
                   "(tau_i = 1e-(i+1) * range)")
@@ -279,7 +284,8 @@ def run_pcz(args, rank, world, device):
     return dict(value=value, ms_step=ms_step, info=info, clocks=clocks, kernels=kernels, launches=launches,
                 roofline={"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
                           "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                          "traffic": None,
+                          "traffic": TRAFFIC.get(dom),
+                          "traffic_source": TRAFFIC_SOURCE if TRAFFIC.get(dom) else None,
                           "algorithmic_bytes_per_launch": int(alg[dom] / max(dom_n, 1)),
                           "ms_per_launch": round(dom_ms / max(dom_n, 1), 4)},
                 e2e=e2e, fields=fields)
