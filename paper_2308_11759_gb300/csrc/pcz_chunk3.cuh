@@ -32,13 +32,14 @@ constexpr int kCompressThreads3 = 512;
 template <typename T>
 constexpr size_t compress_smem3() {
   using S = typename Fmt<T>::S;
-  return (size_t)chunk_buf_words3<T>() * 4      // chunk bit buffer
+  return (size_t)chunk_buf_words3<T>() * 4 * 2  // chunk bit buffers (two components in flight)
          + (size_t)kChunk * 64 * sizeof(S)     // brick buffers, 128 elements per warp
          + (size_t)kChunk * 64 * 8             // plane words of every brick
          + (size_t)kChunk * 64 * 4             // plane code offsets and significance counts
          + 32 * 4 * 5                          // lengths, offsets, modes, escalations, violations
-         + 16                                  // pool base
-         + 32 * 8;                             // per brick: bits of max |x - x~_i|
+         + 16                                  // pool base of the two components in flight
+         + 32 * 8                              // per brick: bits of max |x - x~_i|
+         + 16;                                 // chunk bits of the two components in flight
 }
 
 // R11 group-test bits of one coefficient c that turns significant in plane
@@ -90,6 +91,18 @@ __device__ __forceinline__ void plane_scan(uint64_t W, bool act, int lane, int& 
 // Algorithm 1 on every brick of index chunk `chunk` of a 3D field, all
 // components, by the whole CTA (kCompressThreads3 threads); smem holds
 // compress_smem3<T>() bytes.  Every thread of the CTA must call it.
+// Copies one component's finished chunk from its shared buffer to the pool
+// (base ~0: the pool was too small) and clears the buffer for reuse.
+__device__ __forceinline__ void append_chunk(const CompressParams& P, uint32_t* buf, unsigned long long base,
+                                             int chunk_bits, int tid) {
+  const int nw = (chunk_bits + 63) >> 6;
+  uint64_t* b64 = reinterpret_cast<uint64_t*>(buf);
+  for (int w = tid; w < nw; w += kCompressThreads3) {
+    if (base != ~0ull) P.pool[base + w] = b64[w];
+    b64[w] = 0ull;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t chunk, unsigned char* smem) {
   using F = Fmt<T>;
@@ -104,8 +117,10 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   constexpr bool WIDE = F::P == 64;
   constexpr unsigned FULL = 0xffffffffu;
 
-  uint32_t* cbuf = reinterpret_cast<uint32_t*>(smem);
-  S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4);
+  // component i's bits go to buffer i & 1; it is appended to the pool while
+  // component i + 1 is written, which saves a barrier per component
+  uint32_t* cbufs = reinterpret_cast<uint32_t*>(smem);
+  S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4 * 2);
   uint64_t* s_pw = reinterpret_cast<uint64_t*>(bbuf + kChunk * 64);  // [warp][brick][plane] words
   uint32_t* s_pi = reinterpret_cast<uint32_t*>(s_pw + kChunk * 64);  // [warp][brick][plane] off | n << 16
   int* s_len = reinterpret_cast<int*>(s_pi + kChunk * 64);
@@ -115,6 +130,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   int* s_viol = s_esc + 32;
   unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_viol + 32);
   uint64_t* s_merr = reinterpret_cast<uint64_t*>(s_base + 2);
+  int* s_cbits = reinterpret_cast<int*>(s_merr + 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int h = lane >> 4, t = lane & 15;
@@ -123,7 +139,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   const int64_t b = chunk * kChunk + slot;
   const bool have = b < P.nbricks;
 
-  for (int w = tid; w < BUFW; w += kCompressThreads3) cbuf[w] = 0u;
+  for (int w = tid; w < 2 * BUFW; w += kCompressThreads3) cbufs[w] = 0u;
 
   int64_t bx = 0, by = 0, bz = 0;
   if (have) {
@@ -188,6 +204,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   unsigned pool_nw = 0;
 
   for (int i = 0; i < P.n; ++i) {  // one component per tau_i
+    uint32_t* cbuf = cbufs + (i & 1) * BUFW;
     const U tb = (U)P.tau_bits[i];
     if (any_partial) {  // R4 padding of the residual
       const T last = nvx == 1 ? e[0] : nvx == 2 ? e[1] : nvx == 3 ? e[2] : e[3];
@@ -423,6 +440,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       }
       s_off[lane] = incl - l0;
       const int total = __shfl_sync(FULL, incl, 31);
+      if (lane == 0) s_cbits[i & 1] = total;
       const unsigned nw = (unsigned)((total + 63) >> 6);
       const int md = s_mode[lane];
       const unsigned cz = __popc(__ballot_sync(FULL, md == kModeZero));
@@ -459,7 +477,6 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       }
     }
     __syncthreads();
-    const int chunk_bits = s_off[31] + s_len[31];
 
     // this component's bits of the warp's two bricks, into the chunk buffer
     const uint32_t boff = (uint32_t)s_off[slot];
@@ -509,21 +526,13 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
         atomicOr(P.flags, kFlagPoolOverflow);
         base = ~0ull;
       }
-      *s_base = base;
+      s_base[i & 1] = base;
       P.chunk_pool[(int64_t)i * P.nchunks + chunk] = base;
     }
-    __syncthreads();
-    {  // append the chunk to the pool and clear the buffer for the next
-       // component (its first writes come after two more barriers)
-      const unsigned long long base = *s_base;
-      const int nw = (chunk_bits + 63) >> 6;
-      uint64_t* b64 = reinterpret_cast<uint64_t*>(cbuf);
-      for (int w = tid; w < nw; w += kCompressThreads3) {
-        if (base != ~0ull) P.pool[base + w] = b64[w];
-        b64[w] = 0ull;
-      }
-    }
+    if (i > 0) append_chunk(P, cbufs + ((i - 1) & 1) * BUFW, s_base[(i - 1) & 1], s_cbits[(i - 1) & 1], tid);
   }
+  __syncthreads();
+  append_chunk(P, cbufs + ((P.n - 1) & 1) * BUFW, s_base[(P.n - 1) & 1], s_cbits[(P.n - 1) & 1], tid);
 }
 
 }  // namespace pcz
