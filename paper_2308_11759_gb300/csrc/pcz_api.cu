@@ -55,6 +55,40 @@ struct DevCtx {
 std::mutex g_mu;
 DevCtx g_ctx[128];
 
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[128] = {};
+
+}  // namespace
+
+// The library's own stream-ordered memory pool on the current device.  It
+// keeps freed memory for later calls: the device's default pool hands it back
+// to the driver at every synchronisation, so that the next call would pay
+// for fresh allocations again.
+cudaError_t pcz::scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev & 127]) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pools[dev & 127], &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(g_pools[dev & 127], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = g_pools[dev & 127];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+namespace {
+
 // Stream-ordered device allocation; freed on the same stream.
 struct Scratch {
   std::vector<void*> ptrs;
@@ -62,7 +96,7 @@ struct Scratch {
   explicit Scratch(cudaStream_t st) : s(st) {}
   cudaError_t get(void** p, size_t bytes) {
     *p = nullptr;
-    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
+    cudaError_t e = scratch_alloc(p, bytes ? bytes : 16, s);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }

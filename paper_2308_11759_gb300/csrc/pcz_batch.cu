@@ -662,7 +662,7 @@ pc_status pc_retrieve_batch(int nq, const pc_streams* const* s, const int* k, co
       void* mem = nullptr;
       const size_t jb = align256(sizeof(BoxJob) * G.jobs.size());
       const size_t spill = d == 3 ? 8 * retrieve_spill_words(dt, 3, retrieve_grid(dt, 3, G.units)) : 0;
-      BK(cudaMallocAsync(&mem, jb + spill + 16, st));
+      BK(scratch_alloc(&mem, jb + spill + 16, st));
       cudaError_t e = cudaMemcpyAsync(mem, G.jobs.data(), sizeof(BoxJob) * G.jobs.size(), cudaMemcpyHostToDevice, st);
       RetrieveParams R;
       std::memset(&R, 0, sizeof(R));

@@ -59,5 +59,8 @@ bool tolerances_valid(const double* tau, int n);
 void field_geometry(int ndims, const int64_t* dims, int64_t d3[3], int64_t nb[3], int64_t* nbricks,
                     int64_t* nchunks);
 bool device_pointer(const void* p);
+// Stream-ordered scratch from the library's own memory pool (freed with
+// cudaFreeAsync on a stream).
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
 
 }  // namespace pcz
