@@ -370,6 +370,18 @@ pc_status pc_batch_free(pc_batch *b);
 pc_status pc_retrieve_batch(int nq, const pc_streams *const *s, const int *k, const pc_box *boxes,
                             void *const *d_out, void *cuda_stream);
 
+/*
+ * Debug builds (libpcz_debug.so, compiled with PCZ_DEBUG) check every
+ * shared-memory bit write of the coders and every plane slot and spill index
+ * of the retrieval against its buffer; a failed check skips the access and
+ * sets a bit of a check word instead of faulting.  *word receives the check
+ * bits seen since the last reset (bit 0: 3D chunk buffer, 1: 3D plane tables,
+ * 2: 1D/2D chunk buffer, 3: retrieval plane slots), *enabled (may be NULL) 1
+ * in a debug build and 0 in a release build, where *word is always 0 and no
+ * device call is made.  reset != 0 clears the word.
+ */
+pc_status pc_debug_status(uint32_t *word, int *enabled, int reset);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *pc_last_error(void);
 

@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIBPATH = os.path.join(_HERE, "libpcz.so")
+# PCZ_LIBRARY selects another in-tree build, e.g. libpcz_debug.so (buffer checks)
+LIBPATH = os.environ.get("PCZ_LIBRARY") or os.path.join(_HERE, "libpcz.so")
 
 PC_F32, PC_F64 = 1, 2
 STATUS = {
@@ -85,6 +86,7 @@ def lib():
             "pc_stream_read_index": [vp, C.c_int, u64p, C.POINTER(C.c_uint16), vp],
             "pc_stream_read": [vp, C.c_int, C.c_uint64, C.c_uint64, u64p, vp],
             "pc_server_create": [C.c_uint64, C.c_int, C.c_int, vp, C.POINTER(vp)],
+            "pc_debug_status": [C.POINTER(C.c_uint32), ip, C.c_int],
             "pc_batch_create": [C.c_int, i64p, ip, C.c_int, C.c_int, vp, C.POINTER(vp)],
             "pc_batch_compress": [vp, C.POINTER(vp), dp, C.POINTER(vp)],
             "pc_batch_info": [vp, C.POINTER(BatchInfo)],
@@ -505,6 +507,14 @@ def lossless_sweep(x, delta: int = 4, n_max: int = 64, stream=None):
     tbits = 32 if st.dtype in (_torch().float32,) else 64
     return {"k": k, "bits_per_value": bits, "ratio": (tbits / bits) if bits else None, "measured": meas,
             "streams": st}
+
+
+def debug_status(reset: bool = False):
+    """(check word, enabled): the buffer-check failures a debug build has seen
+    (pc_debug_status); a release build reports (0, False)."""
+    w, en = C.c_uint32(), C.c_int()
+    _check(lib().pc_debug_status(C.byref(w), C.byref(en), 1 if reset else 0))
+    return int(w.value), bool(en.value)
 
 
 KERNEL_KINDS = ("compress", "scan", "pack", "retrieve", "range")

@@ -355,10 +355,24 @@ extern "C" {
 
 const char* pc_last_error(void) { return g_err.c_str(); }
 
+pc_status pc_debug_status(uint32_t* word, int* enabled, int reset) {
+  g_err.clear();
+  if (!word) return fail(PC_ERR_ARG, "word is NULL");
+  *word = check_word_compress(reset) | check_word_small(reset) | check_word_retrieve(reset) |
+          check_word_batch(reset);
+#ifdef PCZ_DEBUG
+  if (enabled) *enabled = 1;
+#else
+  if (enabled) *enabled = 0;
+#endif
+  return PC_OK;
+}
+
 int pc_version(void) { return (int)kFormatVersion; }
 
 pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtype dtype, const double* tau, int n,
                       void* cuda_stream, pc_streams** out) {
+  TraceRange trace_("pc_compress");
   g_err.clear();
   if (!out) return fail(PC_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -589,6 +603,7 @@ static pc_status retrieve_common(const pc_streams* s, int k0, int k, const pc_bo
 }
 
 pc_status pc_retrieve(const pc_streams* s, double tau, int k, const pc_box* box, void* out, void* cuda_stream) {
+  TraceRange trace_("pc_retrieve");
   g_err.clear();
   if (!s || !out) return fail(PC_ERR_ARG, "NULL argument");
   if (tau >= 0) {
@@ -601,6 +616,7 @@ pc_status pc_retrieve(const pc_streams* s, double tau, int k, const pc_box* box,
 }
 
 pc_status pc_refine(const pc_streams* s, int k0, int k, const pc_box* box, void* inout, void* cuda_stream) {
+  TraceRange trace_("pc_refine");
   g_err.clear();
   if (!s || !inout) return fail(PC_ERR_ARG, "NULL argument");
   if (k0 < 0 || k < k0 || k > s->n) return fail(PC_ERR_ARG, "need 0 <= k0 <= k <= n");
@@ -660,6 +676,7 @@ static size_t serialized_size(const pc_streams* s) {
 }
 
 pc_status pc_streams_serialize(const pc_streams* s, void* h_buf, size_t* len, void* cuda_stream) {
+  TraceRange trace_("pc_streams_serialize");
   g_err.clear();
   if (!s || !len) return fail(PC_ERR_ARG, "NULL argument");
   const size_t need = serialized_size(s);
@@ -700,6 +717,7 @@ pc_status pc_streams_serialize(const pc_streams* s, void* h_buf, size_t* len, vo
 }
 
 pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_stream, pc_streams** out) {
+  TraceRange trace_("pc_streams_deserialize");
   g_err.clear();
   if (!h_buf || !out) return fail(PC_ERR_ARG, "NULL argument");
   *out = nullptr;
@@ -896,6 +914,7 @@ pc_status pc_timing_read(double* ms, uint64_t* launches) {
 
 pc_status pc_field_range(const void* d_field, int64_t count, pc_dtype dtype, void* cuda_stream, double* vmin,
                          double* vmax) {
+  TraceRange trace_("pc_field_range");
   g_err.clear();
   if (!d_field || count < 1 || !vmin || !vmax) return fail(PC_ERR_ARG, "bad arguments");
   if (dtype != PC_F32 && dtype != PC_F64) return fail(PC_ERR_ARG, "bad dtype");

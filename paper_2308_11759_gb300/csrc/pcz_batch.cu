@@ -113,6 +113,8 @@ static int batch_grid_t() {
   return grid;
 }
 
+uint32_t check_word_batch(int reset) { return read_check_word(reset); }
+
 int compress_batch_grid(int dtype) { return dtype == 1 ? batch_grid_t<float>() : batch_grid_t<double>(); }
 
 cudaError_t launch_compress_batch(int dtype, const BatchParams* d_bp, int grid, cudaStream_t s) {
@@ -323,6 +325,7 @@ extern "C" {
 
 pc_status pc_batch_create(int nfields, const int64_t* dims, const int* ndims, pc_dtype dtype, int n,
                           void* cuda_stream, pc_batch** out) {
+  TraceRange trace_("pc_batch_create");
   if (!out) return api_fail(PC_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (nfields < 1 || !dims || !ndims) return api_fail(PC_ERR_ARG, "need at least one field, dims and ndims");
@@ -451,6 +454,7 @@ pc_status pc_batch_create(int nfields, const int64_t* dims, const int* ndims, pc
 }
 
 pc_status pc_batch_compress(pc_batch* B, const void* const* d_fields, const double* tau, pc_streams** out) {
+  TraceRange trace_("pc_batch_compress");
   if (!B || !d_fields || !tau || !out) return api_fail(PC_ERR_ARG, "NULL argument");
   const int nf = B->nfields, n = B->n;
   for (int f = 0; f < nf; ++f) {
@@ -626,6 +630,7 @@ pc_status pc_batch_free(pc_batch* B) {
 
 pc_status pc_retrieve_batch(int nq, const pc_streams* const* s, const int* k, const pc_box* boxes,
                             void* const* d_out, void* cuda_stream) {
+  TraceRange trace_("pc_retrieve_batch");
   if (nq < 0 || (nq > 0 && (!s || !k || !d_out))) return api_fail(PC_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // group the queries by (type, dimensionality): one launch per group

@@ -50,12 +50,13 @@ constexpr size_t compress_smem3() {
 // the next token's test bit right after it unless c is the plane's last
 // token, and the plane's first test bit at 0 (set by the token with k = 1).
 // Zeros (runs and the closing test bit) need no write.
-__device__ __forceinline__ void write_token(uint32_t* buf, uint32_t group_base, uint64_t W, int n, int c) {
+__device__ __forceinline__ void write_token(uint32_t* buf, uint32_t cap_bits, uint32_t group_base, uint64_t W,
+                                            int n, int c) {
   const uint64_t before = W & low_mask64(c) & ~low_mask64(n);
   const int k = 1 + __popcll((long long)before);
   const bool last = c >= 63 || (W >> (c + 1)) == 0ull;
-  or_bits(buf, group_base + (uint32_t)(c - n + k), last ? 1ull : 3ull);
-  if (k == 1) atomicOr(buf + (group_base >> 5), 1u << (group_base & 31));
+  or_bits_in(buf, group_base + (uint32_t)(c - n + k), last ? 1ull : 3ull, cap_bits, 0);
+  if (k == 1 && PCZ_CHECK(group_base < cap_bits, 0)) atomicOr(buf + (group_base >> 5), 1u << (group_base & 31));
 }
 
 // Suffix scans of one round of 32 planes (lane l = plane base + l, coded in
@@ -114,6 +115,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   constexpr int HDR = 2 + 3 + F::EBITS;    // mode, escalation, block exponent
   constexpr int LEN_RAW = 2 + N * F::P;
   constexpr int BUFW = chunk_buf_words3<T>();
+  constexpr uint32_t CAP = (uint32_t)BUFW * 32;  // bits of one chunk buffer
   constexpr bool WIDE = F::P == 64;
   constexpr unsigned FULL = 0xffffffffu;
 
@@ -481,24 +483,25 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     // this component's bits of the warp's two bricks, into the chunk buffer
     const uint32_t boff = (uint32_t)s_off[slot];
     if (have && mode == kModeRaw) {
-      if (t == 0) or_bits(cbuf, boff, (uint64_t)kModeRaw);
+      if (t == 0) or_bits_in(cbuf, boff, (uint64_t)kModeRaw, CAP, 0);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) or_bits(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(e[m]));
+      for (int m = 0; m < 4; ++m) or_bits_in(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(e[m]), CAP, 0);
     } else if (have && mode == kModeCoded && t == 0) {
-      or_bits(cbuf, boff, (uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5));
+      or_bits_in(cbuf, boff, (uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5), CAP,
+                 0);
     }
     const int modeA = __shfl_sync(FULL, mode, 0), modeB = __shfl_sync(FULL, mode, 16);
     const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
     // R11: each coded plane's verbatim bits, by the plane's owner lane ...
     if (haveA && modeA == kModeCoded) {
       const uint32_t base = (uint32_t)s_off[warp * 2] + HDR;
-      if (lane >= pA && nA0 > 0) or_bits(cbuf, base + oA0, WA0 & low_mask64(nA0));
-      if (WIDE && lane + 32 >= pA && nA1 > 0) or_bits(cbuf, base + oA1, WA1 & low_mask64(nA1));
+      if (lane >= pA && nA0 > 0) or_bits_in(cbuf, base + oA0, WA0 & low_mask64(nA0), CAP, 0);
+      if (WIDE && lane + 32 >= pA && nA1 > 0) or_bits_in(cbuf, base + oA1, WA1 & low_mask64(nA1), CAP, 0);
     }
     if (haveB && modeB == kModeCoded) {
       const uint32_t base = (uint32_t)s_off[warp * 2 + 1] + HDR;
-      if (lane >= pB && nB0 > 0) or_bits(cbuf, base + oB0, WB0 & low_mask64(nB0));
-      if (WIDE && lane + 32 >= pB && nB1 > 0) or_bits(cbuf, base + oB1, WB1 & low_mask64(nB1));
+      if (lane >= pB && nB0 > 0) or_bits_in(cbuf, base + oB0, WB0 & low_mask64(nB0), CAP, 0);
+      if (WIDE && lane + 32 >= pB && nB1 > 0) or_bits_in(cbuf, base + oB1, WB1 & low_mask64(nB1), CAP, 0);
     }
     // ... and its group-test bits, one token per newly significant coefficient,
     // by the lane that holds the coefficient
@@ -510,9 +513,10 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       for (int j = 0; j < 4; ++j) {
         if ((u[j] >> p) == 0) continue;  // no bit at or above the lowest coded plane
         const int pc = F::P - 1 - F::clz(u[j]);
+        if (!PCZ_CHECK(pc >= 0 && pc < 64, 1)) continue;
         const uint32_t info = pi[pc];
         const int n = (int)(info >> 16), c = t + 16 * j;
-        if (c >= n) write_token(cbuf, base + (info & 0xffffu) + (uint32_t)n, pw[pc], n, c);
+        if (c >= n) write_token(cbuf, CAP, base + (info & 0xffffu) + (uint32_t)n, pw[pc], n, c);
       }
     }
 #pragma unroll

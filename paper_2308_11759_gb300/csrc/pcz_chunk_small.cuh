@@ -74,8 +74,9 @@ __device__ __forceinline__ void lift_inv_brick(S* v) {
 struct SmallWriter {
   uint32_t* buf;
   uint32_t pos;
+  uint32_t cap;  // bits of the buffer
   __device__ __forceinline__ void put(uint64_t v, int nbits) {  // nbits <= 64
-    if (v) or_bits(buf, pos, v & low_mask64(nbits));
+    if (v) or_bits_in(buf, pos, v & low_mask64(nbits), cap, 2);
     pos += (uint32_t)nbits;
   }
 };
@@ -224,7 +225,7 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
         }
       }
       if (pass) {
-        SmallWriter dummy{nullptr, 0};
+        SmallWriter dummy{nullptr, 0, 0};
         const int lenC = HDR + emit_planes<N>(u, F::P, p, dummy, false);
         bool use_raw = false;
         if (lenC > LEN_RAW) {  // R14
@@ -254,7 +255,7 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
     unsigned long long base = 0;
     if (lane == 0 && chunk < P.nchunks) base = nw ? atomicAdd(P.pool_used, (unsigned long long)nw) : 0ull;
     // write the block
-    SmallWriter w{cbuf, (uint32_t)(incl - len)};
+    SmallWriter w{cbuf, (uint32_t)(incl - len), (uint32_t)BUFW * 32};
     if (have && mode == kModeCoded) {
       w.put((uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5), HDR);
       emit_planes<N>(u, F::P, p, w, true);

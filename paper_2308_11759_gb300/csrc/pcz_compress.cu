@@ -52,4 +52,6 @@ cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaS
   return dtype == 1 ? launch_compress_t<float>(p, s) : launch_compress_t<double>(p, s);
 }
 
+uint32_t check_word_compress(int reset) { return read_check_word(reset); }
+
 }  // namespace pcz

@@ -269,6 +269,37 @@ __host__ __device__ constexpr PermTable make_perm(int n) {
 }
 
 // ---------------------------------------------------------------------------
+// Debug builds (-DPCZ_DEBUG) check buffer accesses: a failed check sets bit
+// `site` of this translation unit's check word and skips the access (no trap,
+// so a bad index cannot fault the GPU), and pc_debug_status reports the word.
+// Release builds compile the checks out.  Sites: 0 the 3D chunk bit buffer,
+// 1 the 3D plane tables, 2 the 1D/2D chunk bit buffer, 3 the retrieval plane
+// slots and spill.
+// ---------------------------------------------------------------------------
+#ifdef PCZ_DEBUG
+static __device__ unsigned int g_pcz_check;
+#define PCZ_CHECK(cond, site) ((cond) ? true : (atomicOr(&g_pcz_check, 1u << (site)), false))
+#else
+#define PCZ_CHECK(cond, site) true
+#endif
+
+// This translation unit's check word (0 in release builds); reset clears it.
+static inline uint32_t read_check_word(int reset) {
+#ifdef PCZ_DEBUG
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_pcz_check, sizeof(v)) != cudaSuccess) v = ~0u;
+  if (reset) {
+    const unsigned int z = 0;
+    cudaMemcpyToSymbol(g_pcz_check, &z, sizeof(z));
+  }
+  return v;
+#else
+  (void)reset;
+  return 0;
+#endif
+}
+
+// ---------------------------------------------------------------------------
 // Bit writes into a shared-memory bit buffer (bit b = bit b%32 of word b/32):
 // OR v into bits [off, off + 64).
 // ---------------------------------------------------------------------------
@@ -280,6 +311,14 @@ __device__ __forceinline__ void or_bits(uint32_t* buf, uint32_t off, uint64_t v)
   if ((uint32_t)lo) atomicOr(buf + w, (uint32_t)lo);
   if ((uint32_t)(lo >> 32)) atomicOr(buf + w + 1, (uint32_t)(lo >> 32));
   if (hi) atomicOr(buf + w + 2, hi);
+}
+
+// or_bits into a buffer of cap_bits bits, checked in debug builds.
+__device__ __forceinline__ void or_bits_in(uint32_t* buf, uint32_t off, uint64_t v, uint32_t cap_bits, int site) {
+#ifdef PCZ_DEBUG
+  if (v && !PCZ_CHECK(off + (uint32_t)(64 - __clzll((long long)v)) <= cap_bits, site)) return;
+#endif
+  or_bits(buf, off, v);
 }
 
 // 64 bits of a word stream starting at bit pos (bit b = bit b%64 of word

@@ -8,6 +8,7 @@
 #include <string>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pcz.h"
 #include "pcz_kernels.h"
@@ -38,6 +39,15 @@ struct pc_streams {
 };
 
 namespace pcz {
+
+// An NVTX range over one C-ABI call, for timeline tools (nsys, ncu's range
+// filters); free when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Records msg for pc_last_error() and returns st.
 pc_status api_fail(pc_status st, const std::string& msg);

@@ -134,6 +134,13 @@ cudaError_t launch_brick_offsets(const uint16_t* brick_len, uint32_t* brick_off,
 cudaError_t launch_range(int dtype, const void* x, int64_t count, unsigned long long* enc, unsigned int* flags,
                          cudaStream_t s);
 
+// Check words of the debug build's kernel translation units (always 0 in a
+// release build); reset clears them.
+uint32_t check_word_compress(int reset);
+uint32_t check_word_small(int reset);
+uint32_t check_word_retrieve(int reset);
+uint32_t check_word_batch(int reset);
+
 // Sets the message pc_last_error() returns on this thread.
 void set_last_error(const char* msg);
 

@@ -183,7 +183,7 @@ __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, u
       const int rel = top - pl;
       if (rel < Slots<T>::n)
         slot[rel] = W;
-      else
+      else if (PCZ_CHECK(rel - Slots<T>::n < spill_per_block<T>(), 3))
         spill[rel - Slots<T>::n] = W;
     }
   }
@@ -272,7 +272,8 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
     auto fetch = [&](const BlockMeta& mX, bool cX, const uint64_t* sX, const uint64_t* pX, int pl) {
       if (!cX || pl < mX.p || pl > mX.top) return (uint64_t)0;
       const int rel = mX.top - pl;
-      return rel < Slots<T>::n ? sX[rel] : pX[rel - Slots<T>::n];
+      if (rel < Slots<T>::n) return sX[rel];
+      return PCZ_CHECK(rel - Slots<T>::n < spill_per_block<T>(), 3) ? pX[rel - Slots<T>::n] : (uint64_t)0;
     };
     const uint64_t WA0 = fetch(mA, cA, sA, pA, lane), WB0 = fetch(mB, cB, sB, pB, lane);
     U u[4];
@@ -604,5 +605,7 @@ cudaError_t launch_retrieve(int dtype, int ndims, const RetrieveParams& p, cudaS
   if (ndims != 3) return cudaErrorNotSupported;
   return dtype == 1 ? launch_retrieve_t<float>(p, s) : launch_retrieve_t<double>(p, s);
 }
+
+uint32_t check_word_retrieve(int reset) { return read_check_word(reset); }
 
 }  // namespace pcz

@@ -259,6 +259,7 @@ double seconds_since(Clock::time_point t0) {
 // copies into the callers' buffers, then the slot's completion event.
 pc_status launch_batch(pc_server* S, Slot& sl, const std::vector<Query>& qs, const std::vector<uint64_t>& off,
                        void* const* d_out) {
+  TraceRange trace_("pc_server batch");
   const bool cache = !(S->flags & PC_SERVE_NO_CACHE);
   const int nj = (int)sl.queries.size();
   const pc_dtype dt = qs[sl.queries[0]].dtype;
@@ -411,6 +412,7 @@ pc_status pc_server_reset_cache(pc_server* S) {
 
 pc_status pc_server_replay(pc_server* S, const pc_query* queries, const double* arrival_s, int nq,
                            void* const* d_out, double* latency_s, pc_serve_stats* stats) {
+  TraceRange trace_("pc_server_replay");
   if (!S || (nq > 0 && (!queries || !arrival_s || !latency_s))) return api_fail(PC_ERR_ARG, "NULL argument");
   if (nq < 0) return api_fail(PC_ERR_ARG, "nq < 0");
   if (S->fields.empty() && nq > 0) return api_fail(PC_ERR_ARG, "no fields");

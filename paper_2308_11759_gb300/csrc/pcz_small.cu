@@ -71,4 +71,6 @@ cudaError_t launch_retrieve_small(int dtype, int ndims, const RetrieveParams& p,
   return dtype == 1 ? launch_retrieve_small_t<float, 2>(p, s) : launch_retrieve_small_t<double, 2>(p, s);
 }
 
+uint32_t check_word_small(int reset) { return read_check_word(reset); }
+
 }  // namespace pcz
