@@ -35,6 +35,7 @@ timing barrier.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -128,6 +129,23 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(mhz)}
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (every rank gets it): the whole job is done
+    when the last replica is."""
+    if world <= 1:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world, bytes_per_rank_step, steps, ms_total):
+    """Whole-job throughput: every rank's bytes over the slowest rank's time."""
+    return world * bytes_per_rank_step * steps / (ms_total * 1e-3) / 1e9
 
 
 def make_fields(size, device, dtypes=("f32", "f64")):
@@ -224,14 +242,10 @@ def run_pcz(args, rank, world, device):
     pcz.timing_enable(False)
     if world > 1:
         torch.distributed.barrier()
-    ms_total = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=device, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(t0.elapsed_time(t1), world, device)
     ms_step = ms_total / args.steps
     raw_bytes_step = sum(v["field_bytes"] * (1 + N_COMP) for v in info.values())
-    value = world * raw_bytes_step * args.steps / (ms_total * 1e-3) / 1e9
+    value = job_gbs(world, raw_bytes_step, args.steps, ms_total)
 
     # roofline of the dominant kernel, from its live CUDA-event durations
     hbm, peak_kind = peaks()
@@ -248,6 +262,24 @@ def run_pcz(args, rank, world, device):
             kernels[k] = {"launches": n, "ms_per_launch": round(ms / n, 4), "share": round(ms / ms_total, 4),
                           "gbs_algorithmic": round(alg[k] / (ms * 1e-3) / 1e9, 1) if k in alg and ms > 0 else None}
     launches = sum(n for _, n in ktimes.values())
+
+    # accuracy gain (Sec. 5.1.1): alpha_k = log2(sigma / RMSE_k) - R_k, with R_k the
+    # stream bits per value of components 1..k (index included)
+    gain = {}
+    for name, x in fields.items():
+        st = held[name]
+        x64 = x.double()
+        sigma = float(x64.std())
+        tmp = torch.empty_like(x)
+        rate, al = 0.0, []
+        for k in range(1, N_COMP + 1):
+            _, bits, ib = st.info(k - 1)
+            rate += (bits + 8 * ib) / nvox
+            st.retrieve(k=k, out=tmp)
+            rmse = float(torch.sqrt(torch.mean((x64 - tmp.double()) ** 2)))
+            al.append(round(math.log2(sigma / rmse) - rate, 3) if rmse > 0 else None)
+        gain[name] = al
+        del x64, tmp
 
     # e2e: the same step through host buffers (pinned), copies inside the timed region
     e2e = None
@@ -269,19 +301,15 @@ def run_pcz(args, rank, world, device):
         e1.record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - a
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=device, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(e0.elapsed_time(e1), world, device)
         h2d = sum(v["field_bytes"] for v in info.values())
         d2h = sum(v["field_bytes"] * N_COMP for v in info.values())
-        e2e = {"value": round(world * raw_bytes_step * args.steps / (ems * 1e-3) / 1e9, 3), "unit": "GB/s",
+        e2e = {"value": round(job_gbs(world, raw_bytes_step, args.steps, ems), 3), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems / args.steps, 3),
                "host_wall_s": round(wall, 3)}
     for st in held.values():
         st.close()
-    return dict(value=value, ms_step=ms_step, info=info, clocks=clocks, kernels=kernels, launches=launches,
+    return dict(value=value, ms_step=ms_step, info=info, clocks=clocks, kernels=kernels, launches=launches, gain=gain,
                 roofline={"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
                           "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                           "traffic": TRAFFIC.get(dom),
@@ -585,6 +613,7 @@ def main():
             "kernels": r["kernels"],
             "rates_bits_per_value": {k: v["rates"] for k, v in r["info"].items()},
             "computed_tolerances": {k: v["measured_over_tau"] for k, v in r["info"].items()},
+            "accuracy_gain": r["gain"],
             "lossless": lossless,
             "batched": batched,
             "serving": serving,
