@@ -275,7 +275,19 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
       if (rel < Slots<T>::n) return sX[rel];
       return PCZ_CHECK(rel - Slots<T>::n < spill_per_block<T>(), 3) ? pX[rel - Slots<T>::n] : (uint64_t)0;
     };
-    const uint64_t WA0 = fetch(mA, cA, sA, pA, lane), WB0 = fetch(mB, cB, sB, pB, lane);
+    // lane l fetches plane base + l (and base + 32 + l for 64-bit
+    // coefficients when the coded planes of the pair span more than 32)
+    int base = 0;
+    bool two = WIDE;
+    if constexpr (WIDE) {
+      const int lo = min(cA ? (int)mA.p : 64, cB ? (int)mB.p : 64);
+      const int hi = max(cA ? (int)mA.top : -1, cB ? (int)mB.top : -1);
+      if (hi - lo < 32) {  // one 32-plane window holds every coded plane
+        base = lo;
+        two = false;
+      }
+    }
+    const uint64_t WA0 = fetch(mA, cA, sA, pA, base + lane), WB0 = fetch(mB, cB, sB, pB, base + lane);
     U u[4];
     {
       uint32_t tl[4];
@@ -284,9 +296,9 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
       tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
       tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep);
+      for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep) << base;
     }
-    if constexpr (WIDE) {
+    if (two) {
       const uint64_t WA1 = fetch(mA, cA, sA, pA, lane + 32), WB1 = fetch(mB, cB, sB, pB, lane + 32);
       uint32_t th[4];
       th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
