@@ -84,45 +84,61 @@ struct SmallWriter {
 // R11 for one brick in one thread: plane words are gathered from the
 // coefficients (bit r of plane pl = bit pl of coefficient r); with the
 // significance count n, each plane emits n verbatim bits and then its tokens.
-// Planes above the highest set bit are one 0 test bit each.  Returns the bit
-// length; writes only when write is set.
-template <int N>
-__device__ __forceinline__ int emit_planes(const uint64_t* u, int P, int p, SmallWriter& w, bool write) {
-  uint64_t any = 0;
+// Planes above the highest set bit are one 0 test bit each.
+template <int N, typename U>
+__device__ __forceinline__ int first_empty_plane(const U* u, int p) {
+  U any = 0;
 #pragma unroll
   for (int r = 0; r < N; ++r) any |= u[r];
-  const int top = any ? 63 - __clzll((long long)any) : -1;
-  const int first = max(top + 1, p);  // planes first..P-1 are empty
-  int len = P - first;
-  if (write) w.pos += (uint32_t)len;
+  const int top = any ? (int)(8 * sizeof(U)) - 1 - (sizeof(U) == 8 ? __clzll((long long)any) : __clz((int)any)) : -1;
+  return max(top + 1, p);  // planes from here up to P-1 are empty
+}
+
+template <int N, typename U>
+__device__ __forceinline__ uint32_t plane_word(const U* u, int pl) {
+  uint32_t W = 0;
+#pragma unroll
+  for (int r = 0; r < N; ++r) W |= (uint32_t)((u[r] >> pl) & 1u) << r;
+  return W;
+}
+
+// Bit length of the planes P-1 .. p, one plane at a time in closed form
+// (plane_len), without walking the tokens.
+template <int N, typename U>
+__device__ __forceinline__ int planes_len(const U* u, int P, int p) {
+  const int first = first_empty_plane<N>(u, p);
+  int len = P - first, n = 0;
+  for (int pl = first - 1; pl >= p; --pl) {
+    const uint64_t W = plane_word<N>(u, pl);
+    len += plane_len<N>(W, n);
+    if (n < N && (W >> n)) n = 64 - __clzll((long long)W);
+  }
+  return len;
+}
+
+// Writes the planes P-1 .. p of one brick at w.pos.
+template <int N, typename U>
+__device__ __forceinline__ void emit_planes(const U* u, int P, int p, SmallWriter& w) {
+  const int first = first_empty_plane<N>(u, p);
+  w.pos += (uint32_t)(P - first);  // empty planes: 0 test bits, nothing to write
   int n = 0;
   for (int pl = first - 1; pl >= p; --pl) {
-    uint64_t W = 0;
-#pragma unroll
-    for (int r = 0; r < N; ++r) W |= ((u[r] >> pl) & 1ull) << r;
-    if (n > 0) {
-      if (write) w.put(W, n);
-      len += n;
-    }
+    const uint32_t W = plane_word<N>(u, pl);
+    if (n > 0) w.put(W, n);
     if (n >= N) continue;
-    uint64_t rest = W >> n;
+    uint32_t rest = W >> n;
     for (int it = 0; it < N && n < N; ++it) {
       if (!rest) {  // test 0
-        if (write) w.put(0, 1);
-        len += 1;
+        w.pos += 1;
         break;
       }
-      const int tz = __ffsll((long long)rest) - 1;
-      if (write) {
-        w.put(1, 1);                // test 1
-        w.put(1ull << tz, tz + 1);  // run up to and including the 1
-      }
-      len += tz + 2;
+      const int tz = __ffs((int)rest) - 1;
+      w.put(1, 1);                // test 1
+      w.put(1ull << tz, tz + 1);  // run up to and including the 1
       n += tz + 1;
       rest >>= (tz + 1);
     }
   }
-  return len;
 }
 
 // Algorithm 1 on index chunk `chunk` of a 1D or 2D field, all components, by
@@ -174,12 +190,22 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
 
   for (int i = 0; i < P.n; ++i) {  // one component per tolerance
     const U tb = (U)P.tau_bits[i];
+    // residual e = x - x~ on the in-field lanes; padded lanes copy the nearest
+    // in-field lane along x, then along y (R4), by compile-time indices only
     T e[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {  // residual e = x - x~; padded lanes copy their source (R4)
-      const int ii = k & 3, jj = k >> 2;
-      const int src = min(ii, nvx - 1) + 4 * min(jj, nvy - 1);
-      e[k] = F::sub(x[src], xt[src]);
+    for (int k = 0; k < N; ++k) e[k] = F::sub(x[k], xt[k]);
+#pragma unroll
+    for (int j = 0; j < N / 4; ++j)
+#pragma unroll
+      for (int ii = 1; ii < 4; ++ii)
+        if (ii >= nvx) e[ii + 4 * j] = e[ii - 1 + 4 * j];
+    if constexpr (D == 2) {
+#pragma unroll
+      for (int j = 1; j < 4; ++j)
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+          if (j >= nvy) e[ii + 4 * j] = e[ii + 4 * (j - 1)];
     }
     bool small = true, nf = false;
     int be = 0;
@@ -193,7 +219,7 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
     int mode = kModeZero, esc = 0, p = 0, len = 2;
     const int emax = block_emax_from_be<T>(be);
     const int s = Q - emax;
-    uint64_t u[N];
+    U u[N];
     T xtn[N];
     if (!zero_blk) {
       bool pass = false;
@@ -203,13 +229,13 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
         for (int k = 0; k < N; ++k) q[k] = quantize<T>(F::bits(e[k]), s);  // R6
         lift_fwd_brick<D>(q);                                                // R7
 #pragma unroll
-        for (int r = 0; r < N; ++r) u[r] = (uint64_t)nb_fwd<T>(q[perm_small<D>(r)]);  // R8, R9
+        for (int r = 0; r < N; ++r) u[r] = nb_fwd<T>(q[perm_small<D>(r)]);  // R8, R9
         for (esc = 0;; ++esc) {  // R10, R13
           p = min(max(P.L[i] + s - C - esc, 0), F::P);
           const U keep = p >= F::P ? U(0) : (U)~((U(1) << p) - 1);
           S r[N];
 #pragma unroll
-          for (int rr = 0; rr < N; ++rr) r[perm_small<D>(rr)] = nb_inv<T>((U)u[rr] & keep);
+          for (int rr = 0; rr < N; ++rr) r[perm_small<D>(rr)] = nb_inv<T>((U)(u[rr] & keep));
           lift_inv_brick<D>(r);
           bool ok = true;
 #pragma unroll
@@ -225,8 +251,7 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
         }
       }
       if (pass) {
-        SmallWriter dummy{nullptr, 0, 0};
-        const int lenC = HDR + emit_planes<N>(u, F::P, p, dummy, false);
+        const int lenC = HDR + planes_len<N>(u, F::P, p);
         bool use_raw = false;
         if (lenC > LEN_RAW) {  // R14
           use_raw = true;
@@ -258,7 +283,7 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
     SmallWriter w{cbuf, (uint32_t)(incl - len), (uint32_t)BUFW * 32};
     if (have && mode == kModeCoded) {
       w.put((uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5), HDR);
-      emit_planes<N>(u, F::P, p, w, true);
+      emit_planes<N>(u, F::P, p, w);
     } else if (have && mode == kModeRaw) {
       w.put(kModeRaw, 2);
 #pragma unroll
