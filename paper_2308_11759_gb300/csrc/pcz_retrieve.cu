@@ -275,38 +275,56 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
       if (rel < Slots<T>::n) return sX[rel];
       return PCZ_CHECK(rel - Slots<T>::n < spill_per_block<T>(), 3) ? pX[rel - Slots<T>::n] : (uint64_t)0;
     };
-    // lane l fetches plane base + l (and base + 32 + l for 64-bit
-    // coefficients when the coded planes of the pair span more than 32)
-    int base = 0;
-    bool two = WIDE;
-    if constexpr (WIDE) {
-      const int lo = min(cA ? (int)mA.p : 64, cB ? (int)mB.p : 64);
-      const int hi = max(cA ? (int)mA.top : -1, cB ? (int)mB.top : -1);
-      if (hi - lo < 32) {  // one 32-plane window holds every coded plane
-        base = lo;
-        two = false;
-      }
-    }
-    const uint64_t WA0 = fetch(mA, cA, sA, pA, base + lane), WB0 = fetch(mB, cB, sB, pB, base + lane);
+    const int lo = min(cA ? (int)mA.p : 64, cB ? (int)mB.p : 64);
+    const int hi = max(cA ? (int)mA.top : -1, cB ? (int)mB.top : -1);
     U u[4];
-    {
-      uint32_t tl[4];
-      tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
-      tl[1] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x7632);
-      tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
-      tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
+    if (hi - lo < 16) {
+      // every coded plane of the pair lies in [lo, lo + 16): one transpose
+      // carries two coefficient groups, rows 0-15 the planes of group 2t and
+      // rows 16-31 those of group 2t + 1 (lane l fetches plane lo + (l & 15))
+      const int pl = lo + (lane & 15);
+      const uint64_t WA = fetch(mA, cA, sA, pA, pl), WB = fetch(mB, cB, sB, pB, pl);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep) << base;
-    }
-    if (two) {
-      const uint64_t WA1 = fetch(mA, cA, sA, pA, lane + 32), WB1 = fetch(mB, cB, sB, pB, lane + 32);
-      uint32_t th[4];
-      th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
-      th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
-      th[2] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x5410);
-      th[3] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x7632);
+      for (int t2 = 0; t2 < 2; ++t2) {
+        const int g = 2 * t2 + (lane >> 4);
+        const uint32_t row = (uint32_t)((WA >> (16 * g)) & 0xffffu) | ((uint32_t)((WB >> (16 * g)) & 0xffffu) << 16);
+        const uint32_t w = transpose32(row, lane, tkeep);
+        u[2 * t2] = (U)((U)(w & 0xffffu) << lo);
+        u[2 * t2 + 1] = (U)((U)(w >> 16) << lo);
+      }
+    } else {
+      // lane l fetches plane base + l (and base + 32 + l for 64-bit
+      // coefficients when the coded planes of the pair span more than 32)
+      int base = 0;
+      bool two = WIDE;
+      if constexpr (WIDE) {
+        if (hi - lo < 32) {  // one 32-plane window holds every coded plane
+          base = lo;
+          two = false;
+        }
+      }
+      const uint64_t WA0 = fetch(mA, cA, sA, pA, base + lane), WB0 = fetch(mB, cB, sB, pB, base + lane);
+      {
+        uint32_t tl[4];
+        tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
+        tl[1] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x7632);
+        tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
+        tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) u[j] |= (U)((uint64_t)transpose32(th[j], lane, tkeep) << 32);
+        for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep) << base;
+      }
+      if constexpr (WIDE) {
+        if (two) {
+          const uint64_t WA1 = fetch(mA, cA, sA, pA, lane + 32), WB1 = fetch(mB, cB, sB, pB, lane + 32);
+          uint32_t th[4];
+          th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
+          th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
+          th[2] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x5410);
+          th[3] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x7632);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) u[j] |= (U)((uint64_t)transpose32(th[j], lane, tkeep) << 32);
+        }
+      }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>(u[j]);
