@@ -36,9 +36,9 @@ constexpr size_t compress_smem3() {
          + (size_t)kChunk * 64 * sizeof(S)     // brick buffers, 128 elements per warp
          + (size_t)kChunk * 64 * 8             // plane words of every brick
          + (size_t)kChunk * 64 * 4             // plane code offsets and significance counts
-         + 32 * 4 * 5                          // lengths, offsets, modes, escalations, violations
+         + 2 * 32 * 4 * 4                      // per component parity: lengths, modes, escalations, violations
          + 16                                  // pool base of the two components in flight
-         + 32 * 8                              // per brick: bits of max |x - x~_i|
+         + 2 * 32 * 8                          // per component parity and brick: bits of max |x - x~_i|
          + 16;                                 // chunk bits of the two components in flight
 }
 
@@ -125,14 +125,15 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4 * 2);
   uint64_t* s_pw = reinterpret_cast<uint64_t*>(bbuf + kChunk * 64);  // [warp][brick][plane] words
   uint32_t* s_pi = reinterpret_cast<uint32_t*>(s_pw + kChunk * 64);  // [warp][brick][plane] off | n << 16
-  int* s_len = reinterpret_cast<int*>(s_pi + kChunk * 64);
-  int* s_off = s_len + 32;
-  int* s_mode = s_off + 32;
-  int* s_esc = s_mode + 32;
-  int* s_viol = s_esc + 32;
-  unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_viol + 32);
-  uint64_t* s_merr = reinterpret_cast<uint64_t*>(s_base + 2);
-  int* s_cbits = reinterpret_cast<int*>(s_merr + 32);
+  // per-brick tables, one set per component parity: a warp that runs ahead
+  // into component i + 1 never overwrites what slower warps still read of i
+  int* s_len = reinterpret_cast<int*>(s_pi + kChunk * 64);  // [2][32]
+  int* s_mode = s_len + 64;
+  int* s_esc = s_mode + 64;
+  int* s_viol = s_esc + 64;
+  unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_viol + 64);
+  uint64_t* s_merr = reinterpret_cast<uint64_t*>(s_base + 2);  // [2][32]
+  int* s_cbits = reinterpret_cast<int*>(s_merr + 64);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int h = lane >> 4, t = lane & 15;
@@ -424,32 +425,35 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       merr = y > merr ? y : merr;
     }
 
+    const int par = (i & 1) * 32;
     if (t == 0) {
-      s_len[slot] = blen;
-      s_mode[slot] = have ? mode : -1;
-      s_esc[slot] = (have && mode == kModeCoded) ? esc : 0;
-      s_viol[slot] = have ? viol : 0;
-      s_merr[slot] = have ? (uint64_t)merr : 0ull;
+      s_len[par + slot] = blen;
+      s_mode[par + slot] = have ? mode : -1;
+      s_esc[par + slot] = (have && mode == kModeCoded) ? esc : 0;
+      s_viol[par + slot] = have ? viol : 0;
+      s_merr[par + slot] = have ? (uint64_t)merr : 0ull;
     }
     __syncthreads();
-    if (warp == 0) {  // chunk layout: brick offsets, pool space, index entries
-      const int l0 = s_len[lane];
-      int incl = l0;
+    // chunk layout: every warp scans the 32 brick lengths for its own bricks'
+    // offsets (no second barrier); warp 0 also records the chunk
+    const int l0 = s_len[par + lane];
+    int incl = l0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-      }
-      s_off[lane] = incl - l0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int offA = __shfl_sync(FULL, incl - l0, warp * 2), offB = __shfl_sync(FULL, incl - l0, warp * 2 + 1);
+    if (warp == 0) {
       const int total = __shfl_sync(FULL, incl, 31);
       if (lane == 0) s_cbits[i & 1] = total;
       const unsigned nw = (unsigned)((total + 63) >> 6);
-      const int md = s_mode[lane];
+      const int md = s_mode[par + lane];
       const unsigned cz = __popc(__ballot_sync(FULL, md == kModeZero));
       const unsigned cc = __popc(__ballot_sync(FULL, md == kModeCoded));
       const unsigned cr = __popc(__ballot_sync(FULL, md == kModeRaw));
-      int se = s_esc[lane], sv = s_viol[lane];
-      unsigned long long me = s_merr[lane];
+      int se = s_esc[par + lane], sv = s_viol[par + lane];
+      unsigned long long me = s_merr[par + lane];
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
         se += __shfl_xor_sync(FULL, se, o);
@@ -478,10 +482,9 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
         if (P.brick_off) P.brick_off[(int64_t)i * P.nbricks + bb] = (uint32_t)(incl - l0);
       }
     }
-    __syncthreads();
 
     // this component's bits of the warp's two bricks, into the chunk buffer
-    const uint32_t boff = (uint32_t)s_off[slot];
+    const uint32_t boff = (uint32_t)(h ? offB : offA);
     if (have && mode == kModeRaw) {
       if (t == 0) or_bits_in(cbuf, boff, (uint64_t)kModeRaw, CAP, 0);
 #pragma unroll
@@ -494,12 +497,12 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     const bool haveA = __shfl_sync(FULL, (int)have, 0) != 0, haveB = __shfl_sync(FULL, (int)have, 16) != 0;
     // R11: each coded plane's verbatim bits, by the plane's owner lane ...
     if (haveA && modeA == kModeCoded) {
-      const uint32_t base = (uint32_t)s_off[warp * 2] + HDR;
+      const uint32_t base = (uint32_t)offA + HDR;
       if (lane >= pA && nA0 > 0) or_bits_in(cbuf, base + oA0, WA0 & low_mask64(nA0), CAP, 0);
       if (WIDE && lane + 32 >= pA && nA1 > 0) or_bits_in(cbuf, base + oA1, WA1 & low_mask64(nA1), CAP, 0);
     }
     if (haveB && modeB == kModeCoded) {
-      const uint32_t base = (uint32_t)s_off[warp * 2 + 1] + HDR;
+      const uint32_t base = (uint32_t)offB + HDR;
       if (lane >= pB && nB0 > 0) or_bits_in(cbuf, base + oB0, WB0 & low_mask64(nB0), CAP, 0);
       if (WIDE && lane + 32 >= pB && nB1 > 0) or_bits_in(cbuf, base + oB1, WB1 & low_mask64(nB1), CAP, 0);
     }
