@@ -30,12 +30,6 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const Compre
   compress3_chunk<T>(P, (int64_t)blockIdx.x, smem);
 }
 
-int compress_block_threads(int ndims) { return kCompressThreads3; }
-
-size_t compress_smem_bytes(int dtype, int ndims) {
-  return dtype == 1 ? compress_smem3<float>() : compress_smem3<double>();
-}
-
 template <typename T>
 static cudaError_t launch_compress_t(const CompressParams& p, cudaStream_t s) {
   const size_t smem = compress_smem3<T>();

@@ -144,12 +144,9 @@ uint32_t check_word_batch(int reset);
 // Sets the message pc_last_error() returns on this thread.
 void set_last_error(const char* msg);
 
-// Dynamic shared memory and block shape of the kernels (host-side queries).
-int compress_block_threads(int ndims);
-size_t compress_smem_bytes(int dtype, int ndims);
-int retrieve_block_threads(int ndims);
-// CTAs of a persistent retrieval launch over nbox bricks, and the spill words
-// that launch needs (per CTA).
+// CTAs of a persistent retrieval launch over nunits units, brick pairs per
+// warp of a unit for ncomp components, and the spill words a launch of grid
+// CTAs needs.
 int retrieve_grid(int dtype, int ndims, int64_t nunits);
 int retrieve_unit_mult(int ncomp);
 size_t retrieve_spill_words(int dtype, int ndims, int grid);

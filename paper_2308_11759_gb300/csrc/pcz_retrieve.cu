@@ -579,8 +579,6 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
   }
 }
 
-int retrieve_block_threads(int ndims) { return kRThreads; }
-
 // Brick pairs per warp in a unit (a unit is 16 * umult bricks): as many as
 // keep one round's parse tasks (bricks x components) within kTasks, two per
 // thread, so that warps can steal work; several rounds use 2 pairs per warp.
