@@ -178,11 +178,16 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
   {
     const T* field = reinterpret_cast<const T*>(P.field);
 #pragma unroll
+    for (int j = 0; j < N / 4; ++j) {  // one x-line per row, rows past the field repeat the last (R4)
+      if (have)
+        load_line<T>(field + (4 * by + min(j, nvy - 1)) * P.dims[0] + 4 * bx, nvx, &x[4 * j]);
+      else
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[4 * j + i] = T(0);
+    }
+#pragma unroll
     for (int k = 0; k < N; ++k) {
-      const int i = k & 3, j = k >> 2;
-      const int ci = min(i, nvx - 1), cj = min(j, nvy - 1);
-      x[k] = have ? field[(4 * by + cj) * P.dims[0] + 4 * bx + ci] : T(0);
-      if (have && i < nvx && j < nvy && not_finite<T>(x[k])) bad = true;
+      if (have && (k & 3) < nvx && (k >> 2) < nvy && not_finite<T>(x[k])) bad = true;
       xt[k] = T(0);  // Algorithm 1 starts from x~ = 0
     }
   }
@@ -464,8 +469,7 @@ __device__ __forceinline__ void retrieve_small_brick(const BoxJob& J, int write,
   }
   if (write) {
 #pragma unroll
-    for (int k = 0; k < N; ++k)
-      if (vm[k]) out[oi[k]] = xt[k];
+    for (int j = 0; j < N / 4; ++j) store_line<T>(out + oi[4 * j], &xt[4 * j], &vm[4 * j]);
   }
 }
 
