@@ -224,12 +224,34 @@ __device__ __forceinline__ float dequantize_f32(int32_t q, int s) {
   return __uint_as_float(dequantize_bits<float>(q, s));
 }
 
+// R13 for float64 fields on the FP64 pipe, for kernels whose integer pipe is
+// the busier one: int64 -> double rounding followed by an exact power-of-two
+// scaling is the single correct rounding when 2^-s is a normal double and the
+// result is normal or overflows.  Other cases take the integer path.
+__device__ __forceinline__ double dequantize_f64_fp(int64_t q, int s) {
+  if (q == 0) return 0.0;
+  const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
+  const int nb = 64 - __clzll((long long)a);
+  if (s >= -1023 && s <= 1022 && nb - s >= -1021)
+    return __dmul_rn(__ll2double_rn(q), __longlong_as_double((long long)((uint64_t)(1023 - s) << 52)));
+  return Fmt<double>::val(dequantize_bits<double>(q, s));
+}
+
 template <typename T>
 __device__ __forceinline__ T dequantize_val(typename Fmt<T>::S q, int s) {
   if constexpr (sizeof(T) == 4)
     return dequantize_f32(q, s);
   else
     return Fmt<T>::val(dequantize_bits<T>(q, s));
+}
+
+// dequantize_val with the float64 case on the FP64 pipe (same value).
+template <typename T>
+__device__ __forceinline__ T dequantize_val_fp(typename Fmt<T>::S q, int s) {
+  if constexpr (sizeof(T) == 4)
+    return dequantize_f32(q, s);
+  else
+    return dequantize_f64_fp(q, s);
 }
 
 // |e| <= tau on bit patterns: tb is the pattern of the largest T value not

@@ -348,7 +348,7 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
     lift_inv(r[0], r[1], r[2], r[3]);
     if (my.mode == kModeCoded) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) xi[m] = dequantize_val<T>(r[m], my.s);
+      for (int m = 0; m < 4; ++m) xi[m] = dequantize_val_fp<T>(r[m], my.s);
     }
   }
   if (my.mode == kModeRaw) {
