@@ -52,7 +52,7 @@ N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
 # capture of the current kernels (profiles/retrieve3_compress3_320cube_sections.md).
-TRAFFIC = {"retrieve": 1143594484}
+TRAFFIC = {"retrieve": 1136551264}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 16 retrieval launches of "
                   "the 320^3 case, scaled by the bricks processed to 512^3")
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
