@@ -40,6 +40,7 @@ constexpr int kRWarps = 8;
 constexpr int kRThreads = 32 * kRWarps;
 constexpr int kRound = 8;    // components per round
 constexpr int kTasks = 512;  // parse tasks (block of one brick and component) per round
+constexpr int kTokLut = 512;  // entries of the group-test byte table (2 states x 256 bytes)
 // plane words per block kept in shared memory: as many as let 3 CTAs share an SM
 template <typename T>
 struct Slots {
@@ -60,7 +61,8 @@ template <typename T>
 __host__ __device__ constexpr size_t retrieve_smem3() {
   return (size_t)kTasks * Slots<T>::n * sizeof(uint64_t)  // plane slots
          + (size_t)kTasks * sizeof(BlockMeta)       // block headers
-         + (size_t)kRWarps * 128 * sizeof(typename Fmt<T>::S);  // brick buffers
+         + (size_t)kRWarps * 128 * sizeof(typename Fmt<T>::S)  // brick buffers
+         + (size_t)kTokLut * sizeof(uint16_t);                  // group-test byte table
 }
 
 template <typename T>
@@ -73,12 +75,22 @@ __host__ __device__ constexpr size_t spill_words_per_cta() {
   return (size_t)kTasks * spill_per_block<T>();
 }
 
-// Group-test part of one plane (R11), token by token: a test bit, and on 1
-// the run of coefficient bits up to and including the next 1.  W receives
-// the new coefficients' bits; n and pos advance.  Returns false when a test
-// bit promises a 1 that the run does not hold.
-__device__ __forceinline__ bool parse_tokens_serial(BitReader& br, uint64_t& pos, int& n, uint64_t& W) {
+// Group-test part of one plane (R11), token by token, from bit pos: a test
+// bit, and on 1 the run of coefficient bits up to and including the next 1.
+// With in_run the reader stands inside a run (its test bit already read).
+// W receives the new coefficients' bits; n and pos advance.  Returns false
+// when a run does not end in a 1 within the block's N coefficients.
+__device__ __forceinline__ bool parse_tokens_serial(BitReader& br, uint64_t& pos, int& n, uint64_t& W, bool in_run) {
   constexpr int N = 64;
+  if (in_run) {  // the rest of the current run: its first 1 ends it
+    const uint64_t v = br.peek(pos);
+    if (!v) return false;
+    const int tz = __ffsll((long long)v) - 1;
+    if (n + tz >= N) return false;
+    W |= 1ull << (n + tz);
+    n += tz + 1;
+    pos += (uint64_t)tz + 1;
+  }
   for (int it = 0; it < N && n < N; ++it) {
     const uint64_t v = br.peek(pos);
     if (!(v & 1ull)) {  // test 0: nothing more in this plane
@@ -101,52 +113,77 @@ __device__ __forceinline__ bool parse_tokens_serial(BitReader& br, uint64_t& pos
   return true;
 }
 
-// The same from one 64-bit window g of the stream.  Inside a plane's group
-// part the 1 bits alternate between test bits and run terminators (a test 1
-// is always followed by its run, a run always ends in a 1, and the next test
-// bit follows the terminator at once), so the terminators are the 1 bits of
-// even rank: g & ~prefix_xor(g).  Terminator k (1-based) at bit t marks
-// coefficient n + t - k.  The part ends after the terminator that is not
-// followed by a test 1, or that makes coefficient N - 1 significant.  When the
-// part runs past the window the serial decoder takes over at the next token.
-__device__ __forceinline__ bool parse_tokens(BitReader& br, uint64_t& pos, int& n, uint64_t& W) {
+// Byte table of the group-test part as a two-state machine: in state "test"
+// a 0 ends the part and a 1 starts a run; in state "run" every bit is the
+// next coefficient's bit and a 1 ends the run.  Entry [state][byte] (16 bits):
+// bits 0-7 the 1s among the byte's coefficient bits (coefficient-relative),
+// bits 8-11 their count, bit 12 set when the part ends in the byte; then
+// bits 13-15 hold the bits used up to and including the closing test bit,
+// minus 1; otherwise bit 13 is the state after the byte.
+constexpr uint32_t kTokEnded = 1u << 12;
+
+__device__ __forceinline__ uint16_t token_lut_entry(int idx) {
+  int st = idx >> 8;
+  const int byte = idx & 255;
+  uint32_t out = 0, cnt = 0, e = 0;
+  bool ended = false;
+  for (int j = 0; j < 8 && !ended; ++j) {
+    const int bit = (byte >> j) & 1;
+    if (st == 0) {
+      if (bit) st = 1;
+      else {
+        ended = true;
+        e = kTokEnded | ((uint32_t)j << 13);
+      }
+    } else {
+      out |= (uint32_t)bit << cnt;
+      ++cnt;
+      if (bit) st = 0;
+    }
+  }
+  if (!ended) e = (uint32_t)st << 13;
+  return (uint16_t)(out | (cnt << 8) | e);
+}
+
+// The group-test part of a plane (R11), a byte at a time through the table:
+// n coefficients are significant and the part starts at bit pos.  When a
+// byte would carry the count to N (the last coefficient turns significant,
+// after which no closing test bit follows, or the block is malformed) the
+// serial decoder takes over at that byte.  A valid part is at most
+// 2 (N - n) + 1 <= 129 bits, so 17 bytes bound the loop.
+__device__ __forceinline__ bool parse_group(BitReader& br, uint64_t& pos, int& n, uint64_t& W, const uint16_t* lut) {
   constexpr int N = 64;
-  const uint64_t g = br.peek(pos);
-  if (!(g & 1ull)) {
-    pos += 1;
-    return true;
-  }
-  uint64_t m = g;
-  m ^= m << 1;
-  m ^= m << 2;
-  m ^= m << 4;
-  m ^= m << 8;
-  m ^= m << 16;
-  m ^= m << 32;
-  uint64_t term = g & ~m;
-  const int n0 = n;
-  int k = 0, next = 0;  // tokens decoded; window bit of the next test bit
-  while (term) {
-    const int t = __ffsll((long long)term) - 1;
-    term &= term - 1;
-    ++k;
-    const int c = n0 + t - k;
-    if (c >= N) return false;
-    W |= 1ull << c;
-    n = c + 1;
-    next = t + 1;
-    if (c == N - 1) {  // every coefficient significant: no closing test bit
-      pos += (uint64_t)next;
-      return true;
-    }
-    if (t == 63) break;             // the follower lies beyond the window
-    if (!((g >> (t + 1)) & 1ull)) {  // closing test 0
-      pos += (uint64_t)next + 1;
-      return true;
+  int c = n;
+  uint32_t st = 0;  // state, pre-shifted to index the table's upper half
+  uint32_t used = 0;
+  for (int w = 0; w < 3; ++w) {
+    const uint64_t g = br.peek(pos + used);
+    const uint32_t glo = (uint32_t)g, ghi = (uint32_t)(g >> 32);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (w == 2 && j == 1) return false;  // more than 17 bytes: malformed
+      const uint32_t byte = ((j < 4 ? glo : ghi) >> (8 * (j & 3))) & 0xffu;
+      const uint32_t e = lut[st | byte];
+      const int cn = c + (int)((e >> 8) & 15u);
+      if (cn >= N) {
+        uint64_t q = pos + used;
+        if (!parse_tokens_serial(br, q, c, W, st != 0)) return false;
+        pos = q;
+        n = c;
+        return true;
+      }
+      W |= (uint64_t)(e & 0xffu) << c;
+      c = cn;
+      if (e & kTokEnded) {
+        pos += used + ((e >> 13) & 7u) + 1;
+        n = c;
+        return true;
+      }
+      st = (e >> 5) & 0x100u;
+      used += 8;
     }
   }
-  pos += (uint64_t)next;
-  return parse_tokens_serial(br, pos, n, W);
+  return false;
 }
 
 // R11 decoding of planes P-1 .. p of one block, starting at bit pos and ending
@@ -157,7 +194,7 @@ __device__ __forceinline__ bool parse_tokens(BitReader& br, uint64_t& pos, int& 
 // block; every loop is bounded.
 template <typename T>
 __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, uint64_t* slot, uint64_t* spill,
-                             int& top) {
+                             int& top, const uint16_t* lut) {
   constexpr int N = 64;
   int n = 0;
   top = -1;
@@ -176,7 +213,7 @@ __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, u
       W = br.peek(pos) & low_mask64(n);
       pos += (uint64_t)n;
     }
-    if (n < N && !parse_tokens(br, pos, n, W)) return false;
+    if (n < N && !parse_group(br, pos, n, W, lut)) return false;
     if (pos > end) return false;
     if (W && top < 0) top = pl;
     if (top >= 0) {
@@ -363,7 +400,8 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
 // are not parsed (ZERO).
 template <typename T>
 __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, int64_t unit0, int ub, int base,
-                                           int nc, int L, uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
+                                           int nc, int L, uint64_t* slots, BlockMeta* meta, uint64_t* spill,
+                                           const uint16_t* lut) {
   using F = Fmt<T>;
   constexpr int N = 64;
   constexpr int Q = F::P - 2 - Geo<3>::G;
@@ -406,7 +444,7 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
     if (ok) {
       s = Q - emax;
       p = min(max(cd.L + s - C - esc, 0), F::P);
-      ok = parse_planes<T>(br, off + HDR, end, p, slots + L * Slots<T>::n, spill + L * SP, top);
+      ok = parse_planes<T>(br, off + HDR, end, p, slots + L * Slots<T>::n, spill + L * SP, top, lut);
     }
   } else {
     ok = false;
@@ -431,7 +469,8 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
 // fixed share of long blocks.
 template <typename T>
 __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, int64_t unit0, int ub, int base,
-                                            int nc, int* next, uint64_t* slots, BlockMeta* meta, uint64_t* spill) {
+                                            int nc, int* next, uint64_t* slots, BlockMeta* meta, uint64_t* spill,
+                                            const uint16_t* lut) {
   const int lane = threadIdx.x & 31;
   const int ntask = nc * ub;
   for (;;) {
@@ -439,7 +478,7 @@ __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, 
     if (lane == 0) t0 = atomicAdd(next, 32);
     t0 = __shfl_sync(0xffffffffu, t0, 0);
     if (t0 >= ntask) break;
-    if (t0 + lane < ntask) parse_task<T>(J, err, unit0, ub, base, nc, t0 + lane, slots, meta, spill);
+    if (t0 + lane < ntask) parse_task<T>(J, err, unit0, ub, base, nc, t0 + lane, slots, meta, spill, lut);
   }
 }
 
@@ -454,6 +493,8 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
   uint64_t* slots = reinterpret_cast<uint64_t*>(smem);                // [kTasks][Slots<T>::n]
   BlockMeta* meta = reinterpret_cast<BlockMeta*>(slots + kTasks * Slots<T>::n);  // [kTasks]
   S* bufs = reinterpret_cast<S*>(meta + kTasks);                           // [kRWarps][128]
+  uint16_t* lut = reinterpret_cast<uint16_t*>(bufs + kRWarps * 128);       // [kTokLut]
+  for (int i = threadIdx.x; i < kTokLut; i += kRThreads) lut[i] = token_lut_entry(i);  // read after the loop's first barrier
   __shared__ int s_next;  // next parse task of the round
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, t = lane & 15;
   S* buf = bufs + warp * 128;
@@ -501,7 +542,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       // one round: every warp parses, then each warp rebuilds its umult
       // brick pairs and writes them out
       const int nc = J.k - J.k0;
-      parse_round<T>(J, R.err, unit0, ub, J.k0, nc, &s_next, slots, meta, spill);
+      parse_round<T>(J, R.err, unit0, ub, J.k0, nc, &s_next, slots, meta, spill, lut);
       __syncthreads();
       for (int q = 0; q < umult; ++q) {
         const int uA = 2 * (umult * warp + q);  // unit-local index of the pair's first brick
@@ -542,7 +583,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       }
       for (int base = J.k0; base < J.k; base += kRound) {
         const int nc = min(kRound, J.k - base);
-        parse_round<T>(J, R.err, unit0, 32, base, nc, &s_next, slots, meta, spill);
+        parse_round<T>(J, R.err, unit0, 32, base, nc, &s_next, slots, meta, spill, lut);
         __syncthreads();
         for (int jj = 0; jj < nc; ++jj) {
 #pragma unroll
