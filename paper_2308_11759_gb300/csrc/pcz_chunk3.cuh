@@ -303,12 +303,23 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       lift_inv(r[0], r[1], r[2], r[3]);
       bool ok = true;
       T xtn[4], en[4];
+      if constexpr (sizeof(T) == 4) {
+        T xi[4];
+        dequantize_line<T, false>(r, s, xi);  // x_i = D(y_i)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const T xi = dequantize_val<T>(r[m], s);  // x_i = D(y_i)
-        xtn[m] = F::add(xt[m], xi);               // x~ + x_i (candidate)
-        en[m] = F::sub(x[m], xtn[m]);             // the next residual
-        if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
+        for (int m = 0; m < 4; ++m) {
+          xtn[m] = F::add(xt[m], xi[m]);  // x~ + x_i (candidate)
+          en[m] = F::sub(x[m], xtn[m]);   // the next residual
+          if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const T xi = dequantize_val<T>(r[m], s);  // x_i = D(y_i)
+          xtn[m] = F::add(xt[m], xi);               // x~ + x_i (candidate)
+          en[m] = F::sub(x[m], xtn[m]);             // the next residual
+          if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
+        }
       }
       const bool pass_h = (__ballot_sync(FULL, !ok) & HALF) == 0u;
       if (active) {

@@ -224,19 +224,6 @@ __device__ __forceinline__ float dequantize_f32(int32_t q, int s) {
   return __uint_as_float(dequantize_bits<float>(q, s));
 }
 
-// R13 for float64 fields on the FP64 pipe, for kernels whose integer pipe is
-// the busier one: int64 -> double rounding followed by an exact power-of-two
-// scaling is the single correct rounding when 2^-s is a normal double and the
-// result is normal or overflows.  Other cases take the integer path.
-__device__ __forceinline__ double dequantize_f64_fp(int64_t q, int s) {
-  if (q == 0) return 0.0;
-  const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
-  const int nb = 64 - __clzll((long long)a);
-  if (s >= -1023 && s <= 1022 && nb - s >= -1021)
-    return __dmul_rn(__ll2double_rn(q), __longlong_as_double((long long)((uint64_t)(1023 - s) << 52)));
-  return Fmt<double>::val(dequantize_bits<double>(q, s));
-}
-
 template <typename T>
 __device__ __forceinline__ T dequantize_val(typename Fmt<T>::S q, int s) {
   if constexpr (sizeof(T) == 4)
@@ -245,13 +232,44 @@ __device__ __forceinline__ T dequantize_val(typename Fmt<T>::S q, int s) {
     return Fmt<T>::val(dequantize_bits<T>(q, s));
 }
 
-// dequantize_val with the float64 case on the FP64 pipe (same value).
-template <typename T>
-__device__ __forceinline__ T dequantize_val_fp(typename Fmt<T>::S q, int s) {
-  if constexpr (sizeof(T) == 4)
-    return dequantize_f32(q, s);
-  else
-    return dequantize_f64_fp(q, s);
+// R13 for the 4 values of a line that share the block's scale s.
+//  float: when 2^-s is a normal float, int -> float rounding followed by the
+//    exact multiplication by 2^-s is the single correct rounding for every q
+//    (|q| >= 1 keeps the result normal; overflow gives +-inf as IEEE does;
+//    q = 0 gives +0), so the test is made once per line.
+//  double with EXP: int64 -> double rounding (one rounding), then 2^-s applied
+//    by subtracting s from the exponent field.  For |q| in [1, 2^63] the
+//    rounded value's biased exponent lies in [1023, 1086], so for s in
+//    [-960, 1022] the scaled one lies in [1, 2046]: normal and finite, the
+//    scaling exact, the field never borrows from or carries into the sign.
+//    This spends one conversion instead of some 25 integer instructions, for
+//    kernels whose integer pipe is the busier one.
+//  Other cases take the integer path (dequantize_bits).
+template <typename T, bool EXP>
+__device__ __forceinline__ void dequantize_line(const typename Fmt<T>::S* q, int s, T* v) {
+  if constexpr (sizeof(T) == 4) {
+    if (s >= -127 && s <= 126) {
+      const float sc = __uint_as_float((uint32_t)(127 - s) << 23);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v[m] = __fmul_rn(__int2float_rn(q[m]), sc);
+      return;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v[m] = __uint_as_float(dequantize_bits<float>(q[m], s));
+  } else {
+    if (EXP && s >= -960 && s <= 1022) {
+      const uint32_t adj = (uint32_t)s << 20;  // s in the exponent field of the high word
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const double d = __ll2double_rn(q[m]);
+        const uint32_t hi = (uint32_t)__double2hiint(d);
+        v[m] = __hiloint2double((int)(hi ? hi - adj : 0u), __double2loint(d));  // q = 0 stays +0
+      }
+      return;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v[m] = Fmt<double>::val(dequantize_bits<double>(q[m], s));
+  }
 }
 
 // |e| <= tau on bit patterns: tb is the pattern of the largest T value not

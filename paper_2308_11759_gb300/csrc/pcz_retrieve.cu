@@ -321,10 +321,10 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
       // rows 16-31 those of group 2t + 1 (lane l fetches plane lo + (l & 15))
       const int pl = lo + (lane & 15);
       const uint64_t WA = fetch(mA, cA, sA, pA, pl), WB = fetch(mB, cB, sB, pB, pl);
+      const uint32_t sel = h ? 0x7632u : 0x5410u;  // 16-bit group 2 t2 + h of both words
 #pragma unroll
       for (int t2 = 0; t2 < 2; ++t2) {
-        const int g = 2 * t2 + (lane >> 4);
-        const uint32_t row = (uint32_t)((WA >> (16 * g)) & 0xffffu) | ((uint32_t)((WB >> (16 * g)) & 0xffffu) << 16);
+        const uint32_t row = __byte_perm((uint32_t)(WA >> (32 * t2)), (uint32_t)(WB >> (32 * t2)), sel);
         const uint32_t w = transpose32(row, lane, tkeep);
         u[2 * t2] = (U)((U)(w & 0xffffu) << lo);
         u[2 * t2 + 1] = (U)((U)(w >> 16) << lo);
@@ -383,10 +383,7 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
     for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
     __syncwarp();
     lift_inv(r[0], r[1], r[2], r[3]);
-    if (my.mode == kModeCoded) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) xi[m] = dequantize_val_fp<T>(r[m], my.s);
-    }
+    if (my.mode == kModeCoded) dequantize_line<T, true>(r, my.s, xi);
   }
   if (my.mode == kModeRaw) {
 #pragma unroll
