@@ -48,44 +48,61 @@ constexpr size_t compress_smem3() {
 // plane.  With k its rank among the plane's tokens (1-based), the group part
 // of the plane (which follows the n verbatim bits) holds c's 1 at c - n + k,
 // the next token's test bit right after it unless c is the plane's last
-// token, and the plane's first test bit at 0 (set by the token with k = 1).
-// Zeros (runs and the closing test bit) need no write.
+// token (c + 1 == hi, hi one past the plane word's highest 1), and the
+// plane's first test bit at 0 (set by the token with k = 1).  Zeros (runs and
+// the closing test bit) need no write.  The two bits span at most two words.
 __device__ __forceinline__ void write_token(uint32_t* buf, uint32_t cap_bits, uint32_t group_base, uint64_t W,
-                                            int n, int c) {
+                                            int n, int c, int hi) {
   const uint64_t before = W & low_mask64(c) & ~low_mask64(n);
   const int k = 1 + __popcll((long long)before);
-  const bool last = c >= 63 || (W >> (c + 1)) == 0ull;
-  or_bits_in(buf, group_base + (uint32_t)(c - n + k), last ? 1ull : 3ull, cap_bits, 0);
+  const uint32_t pos = group_base + (uint32_t)(c - n + k);
+  const bool two = c + 1 != hi;
+  if (PCZ_CHECK(pos + (two ? 2u : 1u) <= cap_bits, 0)) {
+    atomicOr(buf + (pos >> 5), (two ? 3u : 1u) << (pos & 31));
+    if (two && (pos & 31) == 31) atomicOr(buf + (pos >> 5) + 1, 1u);
+  }
   if (k == 1 && PCZ_CHECK(group_base < cap_bits, 0)) atomicOr(buf + (group_base >> 5), 1u << (group_base & 31));
 }
 
-// Suffix scans of one round of 32 planes (lane l = plane base + l, coded in
-// descending order): n before each plane (max of the one-past-highest set
-// position over the planes above) and the plane's bit offset.
+// Suffix scans of one round of 32 planes of a warp's two bricks (lane l =
+// plane base + l, coded in descending order): per brick, n before each plane
+// (max of the one-past-highest set position over the planes above), the
+// plane's own one-past-highest position and its bit offset.  The two bricks'
+// offsets share one scan in 16-bit halves (a brick's code is below 2^14 bits).
 template <int N>
-__device__ __forceinline__ void plane_scan(uint64_t W, bool act, int lane, int& cmax, int& csum, int& n_out,
-                                           int& off_out) {
+__device__ __forceinline__ void plane_scan2(uint64_t WA, bool actA, uint64_t WB, bool actB, int lane, int& cmaxA,
+                                            int& cmaxB, uint32_t& csum, int& nA, int& nB, int& hiA, int& hiB,
+                                            int& offA, int& offB) {
   constexpr unsigned FULL = 0xffffffffu;
-  const int hi = (act && W) ? 64 - __clzll((long long)W) : 0;
-  int v = hi;
+  hiA = (actA && WA) ? 64 - __clzll((long long)WA) : 0;
+  hiB = (actB && WB) ? 64 - __clzll((long long)WB) : 0;
+  int vA = hiA, vB = hiB;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_down_sync(FULL, v, o);
-    if (lane + o < 32) v = max(v, y);
+    const int yA = __shfl_down_sync(FULL, vA, o);
+    const int yB = __shfl_down_sync(FULL, vB, o);
+    if (lane + o < 32) {
+      vA = max(vA, yA);
+      vB = max(vB, yB);
+    }
   }
-  int ex = __shfl_down_sync(FULL, v, 1);
-  if (lane == 31) ex = 0;
-  const int n = max(ex, cmax);
-  const int len = act ? plane_len<N>(W, n) : 0;
-  int sum = len;
+  int exA = __shfl_down_sync(FULL, vA, 1);
+  int exB = __shfl_down_sync(FULL, vB, 1);
+  if (lane == 31) exA = exB = 0;
+  nA = max(exA, cmaxA);
+  nB = max(exB, cmaxB);
+  const uint32_t len = (uint32_t)(actA ? plane_len<N>(WA, nA) : 0) | ((uint32_t)(actB ? plane_len<N>(WB, nB) : 0) << 16);
+  uint32_t sum = len;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_down_sync(FULL, sum, o);
+    const uint32_t y = __shfl_down_sync(FULL, sum, o);
     if (lane + o < 32) sum += y;
   }
-  n_out = n;
-  off_out = sum - len + csum;
-  cmax = max(cmax, __shfl_sync(FULL, v, 0));
+  const uint32_t off = sum - len + csum;
+  offA = (int)(off & 0xffffu);
+  offB = (int)(off >> 16);
+  cmaxA = max(cmaxA, __shfl_sync(FULL, vA, 0));
+  cmaxB = max(cmaxB, __shfl_sync(FULL, vB, 0));
   csum += __shfl_sync(FULL, sum, 0);
 }
 
@@ -124,7 +141,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   uint32_t* cbufs = reinterpret_cast<uint32_t*>(smem);
   S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4 * 2);
   uint64_t* s_pw = reinterpret_cast<uint64_t*>(bbuf + kChunk * 64);  // [warp][brick][plane] words
-  uint32_t* s_pi = reinterpret_cast<uint32_t*>(s_pw + kChunk * 64);  // [warp][brick][plane] off | n << 16
+  uint32_t* s_pi = reinterpret_cast<uint32_t*>(s_pw + kChunk * 64);  // [warp][brick][plane] off | n << 14 | hi << 21
   // per-brick tables, one set per component parity: a warp that runs ahead
   // into component i + 1 never overwrites what slower warps still read of i
   int* s_len = reinterpret_cast<int*>(s_pi + kChunk * 64);  // [2][32]
@@ -363,32 +380,32 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     // planes P-1 .. p are coded, from the top: the high round (planes 32 + l)
     // first for 64-bit coefficients, then planes l
     int nA0 = 0, nA1 = 0, nB0 = 0, nB1 = 0, oA0 = 0, oA1 = 0, oB0 = 0, oB1 = 0;
+    int hA0 = 0, hA1 = 0, hB0 = 0, hB1 = 0;
     int totA = 0, totB = 0;
     {
-      int cmax = 0, csum = 0;
-      if constexpr (WIDE) plane_scan<N>(WA1, passA && lane + 32 >= pA, lane, cmax, csum, nA1, oA1);
-      plane_scan<N>(WA0, passA && lane >= pA, lane, cmax, csum, nA0, oA0);
-      totA = csum;
-    }
-    {
-      int cmax = 0, csum = 0;
-      if constexpr (WIDE) plane_scan<N>(WB1, passB && lane + 32 >= pB, lane, cmax, csum, nB1, oB1);
-      plane_scan<N>(WB0, passB && lane >= pB, lane, cmax, csum, nB0, oB0);
-      totB = csum;
+      int cmaxA = 0, cmaxB = 0;
+      uint32_t csum = 0;
+      if constexpr (WIDE)
+        plane_scan2<N>(WA1, passA && lane + 32 >= pA, WB1, passB && lane + 32 >= pB, lane, cmaxA, cmaxB, csum, nA1, nB1,
+                       hA1, hB1, oA1, oB1);
+      plane_scan2<N>(WA0, passA && lane >= pA, WB0, passB && lane >= pB, lane, cmaxA, cmaxB, csum, nA0, nB0, hA0, hB0,
+                     oA0, oB0);
+      totA = (int)(csum & 0xffffu);
+      totB = (int)(csum >> 16);
     }
     const int lenC = HDR + (h ? totB : totA);
     {  // plane p's word, code offset and significance count, for the coefficient lanes
       uint64_t* pw = s_pw + warp * 128;
       uint32_t* pi = s_pi + warp * 128;
       pw[lane] = WA0;
-      pi[lane] = (uint32_t)oA0 | ((uint32_t)nA0 << 16);
+      pi[lane] = (uint32_t)oA0 | ((uint32_t)nA0 << 14) | ((uint32_t)hA0 << 21);
       pw[64 + lane] = WB0;
-      pi[64 + lane] = (uint32_t)oB0 | ((uint32_t)nB0 << 16);
+      pi[64 + lane] = (uint32_t)oB0 | ((uint32_t)nB0 << 14) | ((uint32_t)hB0 << 21);
       if constexpr (WIDE) {
         pw[32 + lane] = WA1;
-        pi[32 + lane] = (uint32_t)oA1 | ((uint32_t)nA1 << 16);
+        pi[32 + lane] = (uint32_t)oA1 | ((uint32_t)nA1 << 14) | ((uint32_t)hA1 << 21);
         pw[96 + lane] = WB1;
-        pi[96 + lane] = (uint32_t)oB1 | ((uint32_t)nB1 << 16);
+        pi[96 + lane] = (uint32_t)oB1 | ((uint32_t)nB1 << 14) | ((uint32_t)hB1 << 21);
       }
     }
 
@@ -529,8 +546,8 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
         const int pc = F::P - 1 - F::clz(u[j]);
         if (!PCZ_CHECK(pc >= 0 && pc < 64, 1)) continue;
         const uint32_t info = pi[pc];
-        const int n = (int)(info >> 16), c = t + 16 * j;
-        if (c >= n) write_token(cbuf, CAP, base + (info & 0xffffu) + (uint32_t)n, pw[pc], n, c);
+        const int n = (int)((info >> 14) & 127u), c = t + 16 * j;
+        if (c >= n) write_token(cbuf, CAP, base + (info & 0x3fffu) + (uint32_t)n, pw[pc], n, c, (int)(info >> 21));
       }
     }
 #pragma unroll
