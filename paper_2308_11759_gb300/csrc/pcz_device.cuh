@@ -376,25 +376,37 @@ __device__ __forceinline__ uint64_t low_mask64(int n) { return n >= 64 ? ~0ull :
 
 // ---------------------------------------------------------------------------
 // 32x32 bit-matrix transpose across a warp: lane l holds row l; afterwards
-// lane l holds column l (bit r = bit l of row r).  Five exchange stages; keep
-// holds this lane's per-stage masks from transpose_masks().
+// lane l holds column l (bit r = bit l of row r).  Five exchange stages with
+// the lane l ^ k, k = 16, 8, 4, 2, 1: a lane keeps the k-bit groups of its
+// word on its own side (low groups when bit k of l is 0) and takes the
+// partner's groups of the other side, shifted across by k.  Stages 16 and 8
+// move whole bytes, so one byte permute does the shift and the merge; stages
+// 4, 2 and 1 use a rotation (the bits it wraps around land in the kept
+// groups and are masked off) and one logic op.  keep[] holds this lane's byte
+// selectors for stages 16 and 8 and its kept-bit masks for stages 4, 2, 1,
+// from transpose_masks().
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void transpose_masks(int lane, uint32_t keep[5]) {
-  const uint32_t lo[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+  keep[0] = (lane & 16) ? 0x3276u : 0x5410u;  // partner's high half down / own low half kept
+  keep[1] = (lane & 8) ? 0x3715u : 0x6240u;   // likewise for the bytes of each half
+  const uint32_t lo[3] = {0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int k = 16 >> st;
-    keep[st] = (lane & k) ? ~lo[st] : lo[st];
+  for (int st = 0; st < 3; ++st) {
+    const int k = 4 >> st;
+    keep[2 + st] = (lane & k) ? ~lo[st] : lo[st];
   }
 }
 
 __device__ __forceinline__ uint32_t transpose32(uint32_t a, int lane, const uint32_t keep[5]) {
+  a = __byte_perm(a, __shfl_xor_sync(0xffffffffu, a, 16), keep[0]);
+  a = __byte_perm(a, __shfl_xor_sync(0xffffffffu, a, 8), keep[1]);
 #pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int k = 16 >> st;
+  for (int st = 0; st < 3; ++st) {
+    const int k = 4 >> st;
     const uint32_t b = __shfl_xor_sync(0xffffffffu, a, k);
-    const uint32_t moved = (lane & k) ? (b >> k) : (b << k);
-    a = (a & keep[st]) | (moved & ~keep[st]);
+    // rotate right by k (partner's high groups down) or by 32 - k (low groups up)
+    const uint32_t moved = __funnelshift_r(b, b, (uint32_t)(2 * (lane & k) - k));
+    a = (a & keep[2 + st]) | (moved & ~keep[2 + st]);
   }
   return a;
 }

@@ -408,7 +408,17 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
   constexpr int SP = spill_per_block<T>();
   const int jj = L / ub;
   const int64_t g = unit0 + L % ub;
-  if (jj >= nc || g >= J.nbox) return;
+  if (jj >= nc) return;
+  if (g >= J.nbox) {  // a unit brick past the box: an empty block, so the rebuild reads every entry
+    BlockMeta bm;
+    bm.off = 0;
+    bm.mode = kModeZero;
+    bm.s = 0;
+    bm.p = 0;
+    bm.top = -1;
+    meta[L] = bm;
+    return;
+  }
   const int64_t bx = J.bl[0] + g % J.bn[0];
   const int64_t r = g / J.bn[0];
   const int64_t b = bx + J.nb[0] * ((J.bl[1] + r % J.bn[1]) + J.nb[1] * (J.bl[2] + r / J.bn[1]));
@@ -483,7 +493,6 @@ template <typename T>
 __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams R) {
   using F = Fmt<T>;
   using S = typename F::S;
-  constexpr unsigned FULL = 0xffffffffu;
   constexpr int SP = spill_per_block<T>();
 
   extern __shared__ __align__(16) unsigned char smem[];
@@ -544,20 +553,11 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       for (int q = 0; q < umult; ++q) {
         const int uA = 2 * (umult * warp + q);  // unit-local index of the pair's first brick
         const BrickLane BL = brick_lane(J, unit0 + uA + h, t);
-        const bool haveA = __shfl_sync(FULL, (int)BL.have, 0) != 0;
-        const bool haveB = __shfl_sync(FULL, (int)BL.have, 16) != 0;
         T xt[4];
         start_sum<T>(J, R.write, BL, xt);
         for (int jj = 0; jj < nc; ++jj) {  // Algorithm 2, components in ascending order
-          BlockMeta mA, mB;
-          mA.mode = mB.mode = kModeZero;
-          mA.s = mB.s = 0;
-          mA.p = mB.p = 0;
-          mA.top = mB.top = -1;
-          mA.off = mB.off = 0;
           const int L = jj * ub + uA;
-          if (haveA) mA = meta[L];
-          if (haveB) mB = meta[L + 1];
+          const BlockMeta mA = meta[L], mB = meta[L + 1];
           T xi[4];
           rebuild_pair<T>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP, spill + (L + 1) * SP,
                           &J.comp[J.k0 + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
@@ -586,17 +586,8 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const int uA = 4 * warp + 2 * q;
-            const bool haveA = __shfl_sync(FULL, (int)BL[q].have, 0) != 0;
-            const bool haveB = __shfl_sync(FULL, (int)BL[q].have, 16) != 0;
-            BlockMeta mA, mB;
-            mA.mode = mB.mode = kModeZero;
-            mA.s = mB.s = 0;
-          mA.p = mB.p = 0;
-            mA.top = mB.top = -1;
-            mA.off = mB.off = 0;
             const int L = jj * 32 + uA;
-            if (haveA) mA = meta[L];
-            if (haveB) mB = meta[L + 1];
+            const BlockMeta mA = meta[L], mB = meta[L + 1];
             T xi[4];
             rebuild_pair<T>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP,
                             spill + (L + 1) * SP, &J.comp[base + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
