@@ -52,9 +52,16 @@ N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
 # capture of the current kernels (profiles/retrieve3_compress3_320cube_sections.md).
-TRAFFIC = {"retrieve": 1136551264}
+TRAFFIC = {"retrieve": 1140794655}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 16 retrieval launches of "
                   "the 320^3 case, scaled by the bricks processed to 512^3")
+# Pipe utilisation of the retrieval kernel (ncu --set full, k = 8 launch of the 320^3 case of
+# this workload, current kernels): it is bound by integer issue, not by HBM.
+PIPES = {"kernel": "retrieve", "launch": "k = 8, 320^3",
+         "alu": {"f32": 0.642, "f64": 0.618}, "fp64": {"f32": 0.0, "f64": 0.559},
+         "issue_active": {"f32": 0.688, "f64": 0.612},
+         "source": "ncu sm__inst_executed_pipe_{alu,fp64}.avg.pct_of_peak_sustained_active, "
+                   "smsp__issue_active.avg.pct_of_peak_sustained_active"}
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
                   "384x384x256 (not multiples of 4), half sums of Gaussians and half k^-5/3 spectra, 6 components "
                   "(tau_i = 1e-(i+1) * range)")
@@ -281,6 +288,36 @@ def run_pcz(args, rank, world, device):
         gain[name] = al
         del x64, tmp
 
+    # progressive sweep (Sec. 4.2): x~_1, then x~_k refined in place from x~_(k-1)
+    # for k = 2..n.  It yields the same n reconstructions as the independent
+    # retrievals of the step, decoding each component once instead of k times.
+    sweep = {}
+    for name, x in fields.items():
+        st = held[name]
+        buf = torch.empty_like(x)
+
+        def sweep_once():
+            st.retrieve(k=1, out=buf)
+            for k in range(2, N_COMP + 1):
+                st.refine(k - 1, k, buf)
+
+        sweep_once()
+        torch.cuda.synchronize()
+        same = bool(torch.equal(buf.view(torch.int32 if x.element_size() == 4 else torch.int64),
+                                outs[name].view(torch.int32 if x.element_size() == 4 else torch.int64)))
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(args.steps):
+            sweep_once()
+        s1.record()
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / args.steps
+        fb = info[name]["field_bytes"]
+        sweep[name] = {"ms": round(ms, 3), "gbs_out": round(N_COMP * fb / (ms * 1e-3) / 1e9, 1),
+                       "equals_independent_k%d" % N_COMP: same}
+        del buf
+
     # e2e: the same step through host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -310,6 +347,7 @@ def run_pcz(args, rank, world, device):
     for st in held.values():
         st.close()
     return dict(value=value, ms_step=ms_step, info=info, clocks=clocks, kernels=kernels, launches=launches, gain=gain,
+                sweep=sweep,
                 roofline={"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
                           "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                           "traffic": TRAFFIC.get(dom),
@@ -607,6 +645,7 @@ def main():
                        "inputs_exceed_l2": True, "l2_flush": False, "parallelism": "replicas"},
             "e2e": r["e2e"],
             "roofline": r["roofline"],
+            "pipe_utilisation": PIPES,
             "cpu_baseline": cpu,
             "clocks": r["clocks"],
             "gpu_launches": r["launches"],
@@ -614,6 +653,8 @@ def main():
             "rates_bits_per_value": {k: v["rates"] for k, v in r["info"].items()},
             "computed_tolerances": {k: v["measured_over_tau"] for k, v in r["info"].items()},
             "accuracy_gain": r["gain"],
+            "progressive_sweep": dict(r["sweep"], note="retrieve k=1 then refine k-1 -> k in place, k = 2..%d; "
+                                      "outside the timed step, not part of value" % N_COMP),
             "lossless": lossless,
             "batched": batched,
             "serving": serving,
