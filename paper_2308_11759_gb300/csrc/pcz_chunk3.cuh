@@ -472,10 +472,22 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       if (lane >= o) incl += y;
     }
     const int offA = __shfl_sync(FULL, incl - l0, warp * 2), offB = __shfl_sync(FULL, incl - l0, warp * 2 + 1);
+    // chunk bookkeeping, spread so that no warp carries much more than the
+    // others to the next barrier: warp 0 sizes the chunk and reserves its
+    // pool space, warp 1 gathers the block counters, and each warp writes its
+    // own bricks' index entries
     if (warp == 0) {
       const int total = __shfl_sync(FULL, incl, 31);
-      if (lane == 0) s_cbits[i & 1] = total;
       const unsigned nw = (unsigned)((total + 63) >> 6);
+      if (lane == 0) {
+        s_cbits[i & 1] = total;
+        // pool space for the chunk; the atomic's result is first needed after
+        // this warp's share of the bit writes, which hides its latency
+        pool_base = nw ? atomicAdd(P.pool_used, (unsigned long long)nw) : 0ull;
+        pool_nw = nw;
+        P.chunk_nwords[(int64_t)i * P.nchunks + chunk] = nw;
+      }
+    } else if (warp == 1) {
       const int md = s_mode[par + lane];
       const unsigned cz = __popc(__ballot_sync(FULL, md == kModeZero));
       const unsigned cc = __popc(__ballot_sync(FULL, md == kModeCoded));
@@ -490,12 +502,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
         me = y > me ? y : me;
       }
       if (lane == 0) {
-        // pool space for the chunk; the atomic's result is first needed after
-        // this warp's share of the bit writes, which hides its latency
-        pool_base = nw ? atomicAdd(P.pool_used, (unsigned long long)nw) : 0ull;
-        pool_nw = nw;
         const int64_t ci = (int64_t)i * P.nchunks + chunk;
-        P.chunk_nwords[ci] = nw;
         uint32_t* cnt = P.chunk_counts + ci * 5;
         cnt[0] = cz;
         cnt[1] = cc;
@@ -504,11 +511,10 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
         cnt[4] = (uint32_t)sv;
         if (P.chunk_maxerr) P.chunk_maxerr[ci] = me;
       }
-      const int64_t bb = chunk * kChunk + lane;
-      if (bb < P.nbricks) {
-        P.brick_len[(int64_t)i * P.nbricks + bb] = (uint16_t)l0;
-        if (P.brick_off) P.brick_off[(int64_t)i * P.nbricks + bb] = (uint32_t)(incl - l0);
-      }
+    }
+    if (t == 0 && have) {
+      P.brick_len[(int64_t)i * P.nbricks + b] = (uint16_t)blen;
+      if (P.brick_off) P.brick_off[(int64_t)i * P.nbricks + b] = (uint32_t)(h ? offB : offA);
     }
 
     // this component's bits of the warp's two bricks, into the chunk buffer
