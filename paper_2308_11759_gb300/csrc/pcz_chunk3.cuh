@@ -330,9 +330,10 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
           if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
         }
       } else {
+        const bool normal = s >= -960 && s <= 1022;  // every result normal and finite
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          const T xi = dequantize_val<T>(r[m], s);  // x_i = D(y_i)
+          const T xi = normal ? Fmt<T>::val(dequantize_f64_normal(r[m], s)) : dequantize_val<T>(r[m], s);  // x_i = D(y_i)
           xtn[m] = F::add(xt[m], xi);               // x~ + x_i (candidate)
           en[m] = F::sub(x[m], xtn[m]);             // the next residual
           if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;

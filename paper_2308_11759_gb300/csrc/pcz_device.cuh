@@ -224,6 +224,24 @@ __device__ __forceinline__ float dequantize_f32(int32_t q, int s) {
   return __uint_as_float(dequantize_bits<float>(q, s));
 }
 
+// R13 for float64 when the result is known to be normal and finite (s in
+// [-960, 1022], see dequantize_line): the 53 leading bits of |q| rounded to
+// nearest, ties to even, by adding half an ulp less one plus the kept lsb
+// before the shift.  A carry out of the 53 bits moves into the exponent field.
+__device__ __forceinline__ uint64_t dequantize_f64_normal(int64_t q, int s) {
+  if (q == 0) return 0ull;
+  const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
+  const int nb = 64 - __clzll((long long)a);  // |q| < 2^nb, so a + half stays below 2^64
+  const int sh = nb - 53;
+  uint64_t r;
+  if (sh > 0)
+    r = (a + ((1ull << (sh - 1)) - 1ull) + ((a >> sh) & 1ull)) >> sh;
+  else
+    r = a << (-sh);
+  const uint64_t bits = ((uint64_t)(nb - s + 1021) << 52) + r;  // r's bit 52 completes the exponent
+  return q < 0 ? (bits | Fmt<double>::SIGN) : bits;
+}
+
 template <typename T>
 __device__ __forceinline__ T dequantize_val(typename Fmt<T>::S q, int s) {
   if constexpr (sizeof(T) == 4)
