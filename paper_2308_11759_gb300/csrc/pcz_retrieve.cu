@@ -41,6 +41,7 @@ constexpr int kRThreads = 32 * kRWarps;
 constexpr int kRound = 8;    // components per round
 constexpr int kTasks = 512;  // parse tasks (block of one brick and component) per round
 constexpr int kTokLut = 512;  // entries of the group-test byte table (2 states x 256 bytes)
+constexpr int kLenBuckets = 64;  // parse tasks are handed out longest block first, by len / 16
 // plane words per block kept in shared memory: as many as let 3 CTAs share an SM
 template <typename T>
 struct Slots {
@@ -48,12 +49,13 @@ struct Slots {
 };
 
 struct BlockMeta {
-  uint64_t off;  // first bit of the brick in the component's payload
-  int16_t s;     // scale exponent (R6), within [-1100, 1100]
-  int8_t p;      // lowest coded plane, 0..64
-  int8_t top;    // highest non-empty plane, -1 if none
+  uint64_t off;   // first bit of the brick in the component's payload
+  int16_t s;      // scale exponent (R6), within [-1100, 1100]
+  uint16_t len;   // bits of the block from the index; 0: nothing to parse (header final)
+  int8_t p;       // lowest coded plane, 0..64
+  int8_t top;     // highest non-empty plane, -1 if none
   int8_t mode;
-  int8_t pad_[3];
+  uint8_t comp;   // component within the round
 };
 static_assert(sizeof(BlockMeta) == 16, "block header size");
 
@@ -62,7 +64,9 @@ __host__ __device__ constexpr size_t retrieve_smem3() {
   return (size_t)kTasks * Slots<T>::n * sizeof(uint64_t)  // plane slots
          + (size_t)kTasks * sizeof(BlockMeta)       // block headers
          + (size_t)kRWarps * 128 * sizeof(typename Fmt<T>::S)  // brick buffers
-         + (size_t)kTokLut * sizeof(uint16_t);                  // group-test byte table
+         + (size_t)kTokLut * sizeof(uint16_t)                   // group-test byte table
+         + (size_t)kTasks * sizeof(uint16_t)                    // parse order of the round's tasks
+         + (size_t)kLenBuckets * sizeof(int);                   // task counts per length bucket
 }
 
 template <typename T>
@@ -392,13 +396,13 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
   }
 }
 
-// Parse task L decodes component base + L / ub of unit brick L % ub (ub =
-// bricks per unit) into slot L.  Components a brick takes from the cache
-// are not parsed (ZERO).
+// Parse task L decodes the block that the round's index pass placed in
+// meta[L] (component base + comp, its first bit and length) into slot L and
+// replaces meta[L] by the block's header.  An entry of length 0 (a brick past
+// the box, or a component the brick takes from the cache) is final already.
 template <typename T>
-__device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, int64_t unit0, int ub, int base,
-                                           int nc, int L, uint64_t* slots, BlockMeta* meta, uint64_t* spill,
-                                           const uint16_t* lut) {
+__device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, int base, int L, uint64_t* slots,
+                                           BlockMeta* meta, uint64_t* spill, const uint16_t* lut) {
   using F = Fmt<T>;
   constexpr int N = 64;
   constexpr int Q = F::P - 2 - Geo<3>::G;
@@ -406,35 +410,11 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
   constexpr int HDR = 2 + 3 + F::EBITS;
   constexpr int EMAXT = (1 << (F::EXPW - 1));  // frexp exponent of the largest finite T
   constexpr int SP = spill_per_block<T>();
-  const int jj = L / ub;
-  const int64_t g = unit0 + L % ub;
-  if (jj >= nc) return;
-  if (g >= J.nbox) {  // a unit brick past the box: an empty block, so the rebuild reads every entry
-    BlockMeta bm;
-    bm.off = 0;
-    bm.mode = kModeZero;
-    bm.s = 0;
-    bm.p = 0;
-    bm.top = -1;
-    meta[L] = bm;
-    return;
-  }
-  const int64_t bx = J.bl[0] + g % J.bn[0];
-  const int64_t r = g / J.bn[0];
-  const int64_t b = bx + J.nb[0] * ((J.bl[1] + r % J.bn[1]) + J.nb[1] * (J.bl[2] + r / J.bn[1]));
-  if (base + jj < cached_level(J, b)) {
-    BlockMeta bm;
-    bm.off = 0;
-    bm.mode = kModeZero;
-    bm.s = 0;
-    bm.p = 0;
-    bm.top = -1;
-    meta[L] = bm;
-    return;
-  }
-  const CompDesc& cd = J.comp[base + jj];
-  const uint64_t off = cd.chunk_word[b / kChunk] * 64ull + cd.brick_off[b];
-  const uint64_t end = off + cd.brick_len[b];
+  const BlockMeta in = meta[L];
+  if (in.len == 0) return;
+  const CompDesc& cd = J.comp[base + in.comp];
+  const uint64_t off = in.off;
+  const uint64_t end = off + in.len;
   BitReader br;
   br.init(cd.payload, cd.nwords, off);
   const uint64_t v = br.peek(off);
@@ -460,8 +440,7 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
     atomicOr(err, 1u);
     mode = kModeZero;
   }
-  BlockMeta bm;
-  bm.off = off;
+  BlockMeta bm = in;
   bm.mode = (int8_t)mode;
   bm.s = (int16_t)s;
   bm.p = (int8_t)p;
@@ -469,23 +448,80 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
   meta[L] = bm;
 }
 
-// Parse phase with warp-granular work stealing: each warp takes the next 32
-// tasks (32 bricks of one component, so the lanes' blocks are alike) until
-// the round's tasks are gone.  Tasks are ordered component-major, the first
-// and costliest component first, so no warp waits at the barrier behind a
-// fixed share of long blocks.
+// Parse phase of a round: task L is component base + L / ub of unit brick
+// L % ub (ub = bricks per unit).
+//  1. Index pass: every thread looks up the index of its tasks (first bit and
+//     length of the block; the loads of the whole round are in flight
+//     together) into meta[L], and counts them per length bucket.
+//  2. A counting sort of the tasks by block length, longest first (each warp
+//     scans the bucket counts itself), into order[].
+//  3. Warp-granular work stealing over order[]: each warp takes the next 32
+//     tasks until none is left.  The 32 blocks a warp parses side by side are
+//     then of alike length, so lanes wait little for one another, and the
+//     short blocks at the end fill the gaps before the barrier.
+// Every thread of the CTA calls it; hist[] is zero on entry and on return.
 template <typename T>
 __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, int64_t unit0, int ub, int base,
                                             int nc, int* next, uint64_t* slots, BlockMeta* meta, uint64_t* spill,
-                                            const uint16_t* lut) {
+                                            const uint16_t* lut, uint16_t* order, int* hist) {
+  constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int ntask = nc * ub;
+  constexpr int PER = kTasks / kRThreads;  // tasks per thread in the index pass
+  int key[PER], rank[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int L = threadIdx.x + q * kRThreads;
+    key[q] = -1;
+    if (L >= ntask) continue;
+    const int jj = L / ub;
+    const int64_t g = unit0 + L % ub;
+    BlockMeta bm;
+    bm.off = 0;
+    bm.s = 0;
+    bm.len = 0;
+    bm.p = 0;
+    bm.top = -1;
+    bm.mode = kModeZero;
+    bm.comp = (uint8_t)jj;
+    if (g < J.nbox) {
+      const int64_t bx = J.bl[0] + g % J.bn[0];
+      const int64_t r = g / J.bn[0];
+      const int64_t b = bx + J.nb[0] * ((J.bl[1] + r % J.bn[1]) + J.nb[1] * (J.bl[2] + r / J.bn[1]));
+      if (base + jj >= cached_level(J, b)) {
+        const CompDesc& cd = J.comp[base + jj];
+        bm.off = cd.chunk_word[b / kChunk] * 64ull + cd.brick_off[b];
+        bm.len = cd.brick_len[b];
+      }
+    }
+    meta[L] = bm;
+    key[q] = kLenBuckets - 1 - min((int)(bm.len >> 4), kLenBuckets - 1);  // longest first
+    rank[q] = atomicAdd(hist + key[q], 1);
+  }
+  __syncthreads();
+  // bucket bases: an exclusive scan of the 64 counts, two per lane, in every warp
+  const int h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
+  int incl = h0 + h1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int b0 = incl - h0 - h1, b1 = incl - h1;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int k = key[q] < 0 ? 0 : key[q];
+    const int e0 = __shfl_sync(FULL, b0, k >> 1), e1 = __shfl_sync(FULL, b1, k >> 1);
+    if (key[q] >= 0) order[((k & 1) ? e1 : e0) + rank[q]] = (uint16_t)(threadIdx.x + q * kRThreads);
+  }
+  __syncthreads();
+  if (threadIdx.x < kLenBuckets) hist[threadIdx.x] = 0;  // read by every warp before the barrier
   for (;;) {
     int t0 = 0;
     if (lane == 0) t0 = atomicAdd(next, 32);
-    t0 = __shfl_sync(0xffffffffu, t0, 0);
+    t0 = __shfl_sync(FULL, t0, 0);
     if (t0 >= ntask) break;
-    if (t0 + lane < ntask) parse_task<T>(J, err, unit0, ub, base, nc, t0 + lane, slots, meta, spill, lut);
+    if (t0 + lane < ntask) parse_task<T>(J, err, base, order[t0 + lane], slots, meta, spill, lut);
   }
 }
 
@@ -500,6 +536,9 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
   BlockMeta* meta = reinterpret_cast<BlockMeta*>(slots + kTasks * Slots<T>::n);  // [kTasks]
   S* bufs = reinterpret_cast<S*>(meta + kTasks);                           // [kRWarps][128]
   uint16_t* lut = reinterpret_cast<uint16_t*>(bufs + kRWarps * 128);       // [kTokLut]
+  uint16_t* order = lut + kTokLut;                                         // [kTasks]
+  int* hist = reinterpret_cast<int*>(order + kTasks);                      // [kLenBuckets]
+  if (threadIdx.x < kLenBuckets) hist[threadIdx.x] = 0;
   for (int i = threadIdx.x; i < kTokLut; i += kRThreads) lut[i] = token_lut_entry(i);  // read after the loop's first barrier
   __shared__ int s_next;  // next parse task of the round
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, t = lane & 15;
@@ -548,7 +587,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       // one round: every warp parses, then each warp rebuilds its umult
       // brick pairs and writes them out
       const int nc = J.k - J.k0;
-      parse_round<T>(J, R.err, unit0, ub, J.k0, nc, &s_next, slots, meta, spill, lut);
+      parse_round<T>(J, R.err, unit0, ub, J.k0, nc, &s_next, slots, meta, spill, lut, order, hist);
       __syncthreads();
       for (int q = 0; q < umult; ++q) {
         const int uA = 2 * (umult * warp + q);  // unit-local index of the pair's first brick
@@ -580,7 +619,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       }
       for (int base = J.k0; base < J.k; base += kRound) {
         const int nc = min(kRound, J.k - base);
-        parse_round<T>(J, R.err, unit0, 32, base, nc, &s_next, slots, meta, spill, lut);
+        parse_round<T>(J, R.err, unit0, 32, base, nc, &s_next, slots, meta, spill, lut, order, hist);
         __syncthreads();
         for (int jj = 0; jj < nc; ++jj) {
 #pragma unroll

@@ -33,6 +33,12 @@ CASES = [
     ("thin_3x5x130_f32", lambda: S.powerlaw((3, 5, 130), seed=9, dtype=np.float32), "bin4", 5),
     ("constant", lambda: np.full((9, 8, 7), 1.5), None, 3),
     ("zeros", lambda: np.zeros((8, 8, 8), dtype=np.float32), None, 2),
+    # white noise: every coefficient significant within the top planes, so a
+    # plane's group-test part runs past one 64-bit window and the last
+    # coefficient turns significant inside a decoded byte
+    ("noise_f32_dense", lambda: _noise((22, 21, 20), 31, np.float32, 0), "dec", 6),
+    # magnitudes spread over 2^-40..1 within each brick, with exact zeros
+    ("noise_f64_wide", lambda: _noise((19, 18, 17), 32, np.float64, 40), "bin8", 8),
     # 2D and 1D fields (4x4 and 4-value bricks)
     ("pl2d_f32_ragged_decade", lambda: S.powerlaw((157, 389), seed=12, dtype=np.float32), "dec", 8),
     ("pl2d_f64_bin4", lambda: S.powerlaw((130, 97), seed=13, dtype=np.float64), "bin4", 10),
@@ -53,10 +59,20 @@ def _steps(shape, seed, dtype):
     return (f + np.where(f > 0.5, 3.0, 0.0)).astype(dtype)
 
 
+def _noise(shape, seed, dtype, spread):
+    """uniform noise in (-1, 1), each value scaled by 2^-U{0..spread}; one value in 16 is 0."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(-1.0, 1.0, size=shape) * np.exp2(-rng.integers(0, spread + 1, size=shape))
+    f[rng.random(shape) < 1.0 / 16] = 0.0
+    return f.astype(dtype)
+
+
 def _tau(x, kind, n):
     if kind is None:
         return [1.0 / (i + 1) for i in range(n)]
     r = O.value_range(x)
+    if kind == "bin8":
+        return O.tau_binary(r, 8, n)
     return O.tau_binary(r, 4, n) if kind == "bin4" else O.tau_decade(r, n)
 
 
@@ -68,7 +84,7 @@ def pair(request, P):
     xd = torch.from_numpy(x).cuda()
     if kind is not None:  # the product's own schedule from the device range is the oracle's, bit for bit
         r = P.value_range(xd)
-        gt = P.tau_binary(r, 4, n) if kind == "bin4" else P.tau_decade(r, n)
+        gt = P.tau_binary(r, {"bin4": 4, "bin8": 8}[kind], n) if kind.startswith("bin") else P.tau_decade(r, n)
         assert gt == tau
     gpu = P.compress(xd, tau)
     ref = O.Streams(x, tau, nthreads=4)
