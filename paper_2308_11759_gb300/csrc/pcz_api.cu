@@ -278,6 +278,18 @@ pc_status box_of(const pc_streams* s, const pc_box* box, int64_t lo[3], int64_t 
   return PC_OK;
 }
 
+// Magic numbers of DivMagic for divisor d (1 <= d < 2^32).
+DivMagic div_magic(uint64_t d) {
+  int l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  DivMagic D;
+  D.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  D.s1 = (uint8_t)(l ? 1 : 0);
+  D.s2 = (uint8_t)(l ? l - 1 : 0);
+  D.pad_ = 0;
+  return D;
+}
+
 // One retrieval job over the box of a stream set (units not yet placed).
 BoxJob make_job(const pc_streams* s, int k0, int k, const int64_t lo[3], const int64_t hi[3], void* d_out) {
   BoxJob J;
@@ -295,6 +307,11 @@ BoxJob make_job(const pc_streams* s, int k0, int k, const int64_t lo[3], const i
   J.k0 = k0;
   J.k = k;
   J.umult = retrieve_unit_mult(k - k0);
+  if (J.nbox < (1ll << 32)) {
+    J.dv_bn0 = div_magic((uint64_t)J.bn[0]);
+    J.dv_bn1 = div_magic((uint64_t)J.bn[1]);
+  }
+  J.dv_ub = div_magic(16ull * (uint64_t)J.umult);
   J.out = d_out;
   return J;
 }

@@ -46,6 +46,17 @@ struct CompDesc {
 // One box of one field for the retrieval kernel (Algorithm 2 on the bricks
 // that meet the box, components k0+1..k).  A launch runs a list of jobs, each
 // on its own units of bricks.
+// Division of 32-bit unsigned n by an invariant d >= 1 with one high
+// multiply (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): t = mulhi(m, n), n / d = (t + ((n - t) >> s1)) >> s2
+// with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, s1 = min(l, 1),
+// s2 = max(l - 1, 0).  Exact for every n and d below 2^32.
+struct DivMagic {
+  uint32_t m;
+  uint8_t s1, s2;
+  uint16_t pad_;
+};
+
 struct BoxJob {
   const CompDesc* comp;          // device array of the field's n descriptors
   int64_t dims[3], nb[3];
@@ -56,6 +67,9 @@ struct BoxJob {
   int k0, k;
   int umult;                     // a unit is 16 * umult bricks
   int pad_;
+  DivMagic dv_bn0, dv_bn1;       // division by bn[0] and bn[1] (used when nbox < 2^32)
+  DivMagic dv_ub;                // division by the bricks of a unit, 16 * umult
+  int32_t pad2_[2];
   void* out;                     // box values of T (read too when k0 > 0)
   const void* cache;             // full-field cached partial sums of T, or null
   const uint8_t* level;          // per brick: k of the cached partial sum (0: none)

@@ -59,6 +59,12 @@ struct BlockMeta {
 };
 static_assert(sizeof(BlockMeta) == 16, "block header size");
 
+// n / d for an invariant d, by one high multiply (DivMagic).
+__device__ __forceinline__ uint32_t div_by(uint32_t n, const DivMagic& D) {
+  const uint32_t t = __umulhi(D.m, n);
+  return (t + ((n - t) >> D.s1)) >> D.s2;
+}
+
 template <typename T>
 __host__ __device__ constexpr size_t retrieve_smem3() {
   return (size_t)kTasks * Slots<T>::n * sizeof(uint64_t)  // plane slots
@@ -79,12 +85,57 @@ __host__ __device__ constexpr size_t spill_words_per_cta() {
   return (size_t)kTasks * spill_per_block<T>();
 }
 
+// Sequential reader of one block's bits with 32-bit positions relative to
+// the start of the word that holds the block's first bit: the two current
+// words in 32-bit halves, one load per 64 bits consumed, and a 64-bit window
+// at any position made of two funnel shifts.  Words at or beyond the
+// payload's end read as zero.  Positions must not decrease.
+struct BlockBits {
+  const uint64_t* __restrict__ w;  // the payload from the block's first word
+  uint32_t nw;                     // words readable from w
+  uint32_t wi;                     // index of the word in a0:a1
+  uint32_t a0, a1, b0, b1;         // words wi and wi + 1
+  __device__ __forceinline__ uint64_t ld(uint32_t i) const { return i < nw ? __ldg(w + i) : 0ull; }
+  __device__ __forceinline__ void set(uint64_t lo, uint64_t hi) {
+    a0 = (uint32_t)lo;
+    a1 = (uint32_t)(lo >> 32);
+    b0 = (uint32_t)hi;
+    b1 = (uint32_t)(hi >> 32);
+  }
+  // bit position of the block's first bit within the reader's frame: off & 63
+  __device__ __forceinline__ void init(const uint64_t* words, uint64_t nwords, uint64_t off) {
+    const uint64_t w0 = off >> 6;
+    w = words + w0;
+    nw = w0 < nwords ? (uint32_t)min(nwords - w0, (uint64_t)0xffffffffu) : 0u;
+    wi = 0;
+    set(ld(0), ld(1));
+  }
+  __device__ __forceinline__ uint64_t peek(uint32_t pos) {
+    const uint32_t i = pos >> 6;
+    if (i != wi) {
+      if (i == wi + 1) {
+        a0 = b0;
+        a1 = b1;
+        const uint64_t nb = ld(i + 1);
+        b0 = (uint32_t)nb;
+        b1 = (uint32_t)(nb >> 32);
+      } else {
+        set(ld(i), ld(i + 1));
+      }
+      wi = i;
+    }
+    const bool up = pos & 32u;  // window starts in the word's upper half
+    const uint32_t x0 = up ? a1 : a0, x1 = up ? b0 : a1, x2 = up ? b1 : b0;
+    return ((uint64_t)__funnelshift_r(x1, x2, pos) << 32) | __funnelshift_r(x0, x1, pos);
+  }
+};
+
 // Group-test part of one plane (R11), token by token, from bit pos: a test
 // bit, and on 1 the run of coefficient bits up to and including the next 1.
 // With in_run the reader stands inside a run (its test bit already read).
 // W receives the new coefficients' bits; n and pos advance.  Returns false
 // when a run does not end in a 1 within the block's N coefficients.
-__device__ __forceinline__ bool parse_tokens_serial(BitReader& br, uint64_t& pos, int& n, uint64_t& W, bool in_run) {
+__device__ __forceinline__ bool parse_tokens_serial(BlockBits& br, uint32_t& pos, int& n, uint64_t& W, bool in_run) {
   constexpr int N = 64;
   if (in_run) {  // the rest of the current run: its first 1 ends it
     const uint64_t v = br.peek(pos);
@@ -93,7 +144,7 @@ __device__ __forceinline__ bool parse_tokens_serial(BitReader& br, uint64_t& pos
     if (n + tz >= N) return false;
     W |= 1ull << (n + tz);
     n += tz + 1;
-    pos += (uint64_t)tz + 1;
+    pos += (uint32_t)tz + 1;
   }
   for (int it = 0; it < N && n < N; ++it) {
     const uint64_t v = br.peek(pos);
@@ -112,7 +163,7 @@ __device__ __forceinline__ bool parse_tokens_serial(BitReader& br, uint64_t& pos
     if (n + tz >= N) return false;
     W |= 1ull << (n + tz);
     n += tz + 1;
-    pos += (uint64_t)tz + 2;
+    pos += (uint32_t)tz + 2;
   }
   return true;
 }
@@ -155,7 +206,7 @@ __device__ __forceinline__ uint16_t token_lut_entry(int idx) {
 // after which no closing test bit follows, or the block is malformed) the
 // serial decoder takes over at that byte.  A valid part is at most
 // 2 (N - n) + 1 <= 129 bits, so 17 bytes bound the loop.
-__device__ __forceinline__ bool parse_group(BitReader& br, uint64_t& pos, int& n, uint64_t& W, const uint16_t* lut) {
+__device__ __forceinline__ bool parse_group(BlockBits& br, uint32_t& pos, int& n, uint64_t& W, const uint16_t* lut) {
   constexpr int N = 64;
   int c = n;
   uint32_t st = 0;  // state, pre-shifted to index the table's upper half
@@ -170,7 +221,7 @@ __device__ __forceinline__ bool parse_group(BitReader& br, uint64_t& pos, int& n
       const uint32_t e = lut[st | byte];
       const int cn = c + (int)((e >> 8) & 15u);
       if (cn >= N) {
-        uint64_t q = pos + used;
+        uint32_t q = pos + used;
         if (!parse_tokens_serial(br, q, c, W, st != 0)) return false;
         pos = q;
         n = c;
@@ -197,7 +248,7 @@ __device__ __forceinline__ bool parse_group(BitReader& br, uint64_t& pos, int& n
 // test bit each and are skipped together.  Returns false on a malformed
 // block; every loop is bounded.
 template <typename T>
-__device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, uint64_t* slot, uint64_t* spill,
+__device__ bool parse_planes(BlockBits& br, uint32_t pos, uint32_t end, int p, uint64_t* slot, uint64_t* spill,
                              int& top, const uint16_t* lut) {
   constexpr int N = 64;
   int n = 0;
@@ -208,14 +259,14 @@ __device__ bool parse_planes(BitReader& br, uint64_t pos, uint64_t end, int p, u
     if (v & 1ull) break;
     const int z = v ? __ffsll((long long)v) - 1 : 64;
     const int skip = min(z, pl - p + 1);
-    pos += (uint64_t)skip;
+    pos += (uint32_t)skip;
     pl -= skip;
   }
   for (; pl >= p; --pl) {
     uint64_t W = 0;
     if (n > 0) {
       W = br.peek(pos) & low_mask64(n);
-      pos += (uint64_t)n;
+      pos += (uint32_t)n;
     }
     if (n < N && !parse_group(br, pos, n, W, lut)) return false;
     if (pos > end) return false;
@@ -413,17 +464,16 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
   const BlockMeta in = meta[L];
   if (in.len == 0) return;
   const CompDesc& cd = J.comp[base + in.comp];
-  const uint64_t off = in.off;
-  const uint64_t end = off + in.len;
-  BitReader br;
-  br.init(cd.payload, cd.nwords, off);
-  const uint64_t v = br.peek(off);
+  BlockBits br;  // positions from the start of the block's first word
+  br.init(cd.payload, cd.nwords, in.off);
+  const uint32_t start = (uint32_t)(in.off & 63u), end = start + in.len;
+  const uint64_t v = br.peek(start);
   int mode = (int)(v & 3ull), s = 0, p = 0, top = -1;
   bool ok;
   if (mode == kModeZero) {
-    ok = end == off + 2;
+    ok = in.len == 2;
   } else if (mode == kModeRaw) {
-    ok = end == off + 2 + (uint64_t)N * F::P;
+    ok = in.len == 2 + N * F::P;
   } else if (mode == kModeCoded) {
     const int esc = (int)((v >> 2) & 7ull);
     const int emax = (int)((v >> 5) & ((1ull << F::EBITS) - 1)) - F::EBIAS;
@@ -431,7 +481,7 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
     if (ok) {
       s = Q - emax;
       p = min(max(cd.L + s - C - esc, 0), F::P);
-      ok = parse_planes<T>(br, off + HDR, end, p, slots + L * Slots<T>::n, spill + L * SP, top, lut);
+      ok = parse_planes<T>(br, start + HDR, end, p, slots + L * Slots<T>::n, spill + L * SP, top, lut);
     }
   } else {
     ok = false;
@@ -474,8 +524,8 @@ __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, 
     const int L = threadIdx.x + q * kRThreads;
     key[q] = -1;
     if (L >= ntask) continue;
-    const int jj = L / ub;
-    const int64_t g = unit0 + L % ub;
+    const int jj = (int)div_by((uint32_t)L, J.dv_ub);  // ub = 16 * umult
+    const int64_t g = unit0 + (L - jj * ub);
     BlockMeta bm;
     bm.off = 0;
     bm.s = 0;
@@ -485,9 +535,21 @@ __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, 
     bm.mode = kModeZero;
     bm.comp = (uint8_t)jj;
     if (g < J.nbox) {
-      const int64_t bx = J.bl[0] + g % J.bn[0];
-      const int64_t r = g / J.bn[0];
-      const int64_t b = bx + J.nb[0] * ((J.bl[1] + r % J.bn[1]) + J.nb[1] * (J.bl[2] + r / J.bn[1]));
+      int64_t bx, by, bz;
+      if (J.nbox < (1ll << 32)) {  // 32-bit division by the box's invariant extents
+        const uint32_t g32 = (uint32_t)g;
+        const uint32_t r = div_by(g32, J.dv_bn0);
+        const uint32_t z = div_by(r, J.dv_bn1);
+        bx = J.bl[0] + (int64_t)(g32 - r * (uint32_t)J.bn[0]);
+        by = J.bl[1] + (int64_t)(r - z * (uint32_t)J.bn[1]);
+        bz = J.bl[2] + (int64_t)z;
+      } else {
+        bx = J.bl[0] + g % J.bn[0];
+        const int64_t r = g / J.bn[0];
+        by = J.bl[1] + r % J.bn[1];
+        bz = J.bl[2] + r / J.bn[1];
+      }
+      const int64_t b = bx + J.nb[0] * (by + J.nb[1] * bz);
       if (base + jj >= cached_level(J, b)) {
         const CompDesc& cd = J.comp[base + jj];
         bm.off = cd.chunk_word[b / kChunk] * 64ull + cd.brick_off[b];
