@@ -258,8 +258,22 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     const int emax = block_emax_from_be<T>(be);
     const int s = Q - emax;
     S q[4];
+    bool qdone = false;
+    if constexpr (sizeof(T) == 4) {
+      if (s >= -126 && s <= 127) {
+        // 2^s is a normal float: e * 2^s is exact whenever |q| >= 1 (at most
+        // 2^Q, no overflow; a product below the normal range truncates to 0
+        // either way), so truncating the product is the R6 quantisation
+        const float sc = __uint_as_float((uint32_t)(127 + s) << 23);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) q[m] = quantize<T>(F::bits(e[m]), s);
+        for (int m = 0; m < 4; ++m) q[m] = __float2int_rz(__fmul_rn(e[m], sc));
+        qdone = true;
+      }
+    }
+    if (!qdone) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) q[m] = quantize<T>(F::bits(e[m]), s);
+    }
 
     // R7: lifting along x (in the lane), y and z (shared buffer)
     lift_fwd(q[0], q[1], q[2], q[3]);

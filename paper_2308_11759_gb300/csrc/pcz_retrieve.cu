@@ -290,15 +290,28 @@ struct BrickLane {
   int64_t bx, b, orow, frow;
 };
 
+// FAST_DIV: split g by invariant-integer division (measured faster for
+// float64 fields and slower for float32 ones, where the kernel's register
+// allocation changes with it).
+template <bool FAST_DIV>
 __device__ __forceinline__ BrickLane brick_lane(const BoxJob& J, int64_t g, int t) {
   BrickLane L;
   L.have = g < J.nbox;
   int64_t bx = 0, by = 0, bz = 0;
   if (L.have) {
-    bx = J.bl[0] + g % J.bn[0];
-    const int64_t r = g / J.bn[0];
-    by = J.bl[1] + r % J.bn[1];
-    bz = J.bl[2] + r / J.bn[1];
+    if (FAST_DIV && J.nbox < (1ll << 32)) {  // 32-bit division by the box's invariant extents
+      const uint32_t g32 = (uint32_t)g;
+      const uint32_t r = div_by(g32, J.dv_bn0);
+      const uint32_t z = div_by(r, J.dv_bn1);
+      bx = J.bl[0] + (int64_t)(g32 - r * (uint32_t)J.bn[0]);
+      by = J.bl[1] + (int64_t)(r - z * (uint32_t)J.bn[1]);
+      bz = J.bl[2] + (int64_t)z;
+    } else {
+      bx = J.bl[0] + g % J.bn[0];
+      const int64_t r = g / J.bn[0];
+      by = J.bl[1] + r % J.bn[1];
+      bz = J.bl[2] + r / J.bn[1];
+    }
   }
   L.bx = bx;
   L.b = bx + J.nb[0] * (by + J.nb[1] * bz);
@@ -653,7 +666,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       __syncthreads();
       for (int q = 0; q < umult; ++q) {
         const int uA = 2 * (umult * warp + q);  // unit-local index of the pair's first brick
-        const BrickLane BL = brick_lane(J, unit0 + uA + h, t);
+        const BrickLane BL = brick_lane<sizeof(T) == 8>(J, unit0 + uA + h, t);
         T xt[4];
         start_sum<T>(J, R.write, BL, xt);
         for (int jj = 0; jj < nc; ++jj) {  // Algorithm 2, components in ascending order
@@ -676,7 +689,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
       T xt[2][4];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        BL[q] = brick_lane(J, unit0 + 4 * warp + 2 * q + h, t);
+        BL[q] = brick_lane<sizeof(T) == 8>(J, unit0 + 4 * warp + 2 * q + h, t);
         start_sum<T>(J, R.write, BL[q], xt[q]);
       }
       for (int base = J.k0; base < J.k; base += kRound) {
