@@ -130,44 +130,6 @@ struct BlockBits {
   }
 };
 
-// Group-test part of one plane (R11), token by token, from bit pos: a test
-// bit, and on 1 the run of coefficient bits up to and including the next 1.
-// With in_run the reader stands inside a run (its test bit already read).
-// W receives the new coefficients' bits; n and pos advance.  Returns false
-// when a run does not end in a 1 within the block's N coefficients.
-__device__ __forceinline__ bool parse_tokens_serial(BlockBits& br, uint32_t& pos, int& n, uint64_t& W, bool in_run) {
-  constexpr int N = 64;
-  if (in_run) {  // the rest of the current run: its first 1 ends it
-    const uint64_t v = br.peek(pos);
-    if (!v) return false;
-    const int tz = __ffsll((long long)v) - 1;
-    if (n + tz >= N) return false;
-    W |= 1ull << (n + tz);
-    n += tz + 1;
-    pos += (uint32_t)tz + 1;
-  }
-  for (int it = 0; it < N && n < N; ++it) {
-    const uint64_t v = br.peek(pos);
-    if (!(v & 1ull)) {  // test 0: nothing more in this plane
-      pos += 1;
-      return true;
-    }
-    const uint64_t rest = v >> 1;
-    int tz;
-    if (rest) {
-      tz = __ffsll((long long)rest) - 1;
-    } else {
-      if (!(br.peek(pos + 64) & 1ull)) return false;
-      tz = 63;
-    }
-    if (n + tz >= N) return false;
-    W |= 1ull << (n + tz);
-    n += tz + 1;
-    pos += (uint32_t)tz + 2;
-  }
-  return true;
-}
-
 // Byte table of the group-test part as a two-state machine: in state "test"
 // a 0 ends the part and a 1 starts a run; in state "run" every bit is the
 // next coefficient's bit and a 1 ends the run.  Entry [state][byte] (16 bits):
@@ -202,10 +164,10 @@ __device__ __forceinline__ uint16_t token_lut_entry(int idx) {
 
 // The group-test part of a plane (R11), a byte at a time through the table:
 // n coefficients are significant and the part starts at bit pos.  When a
-// byte would carry the count to N (the last coefficient turns significant,
-// after which no closing test bit follows, or the block is malformed) the
-// serial decoder takes over at that byte.  A valid part is at most
-// 2 (N - n) + 1 <= 129 bits, so 17 bytes bound the loop.
+// byte would carry the count to N, the last coefficient turns significant in
+// it (after which no closing test bit follows) or the block is malformed; the
+// part's end then follows from the byte's entry in closed form.  A valid part
+// is at most 2 (N - n) + 1 <= 129 bits, so 17 bytes bound the loop.
 __device__ __forceinline__ bool parse_group(BlockBits& br, uint32_t& pos, int& n, uint64_t& W, const uint16_t* lut) {
   constexpr int N = 64;
   int c = n;
@@ -221,10 +183,16 @@ __device__ __forceinline__ bool parse_group(BlockBits& br, uint32_t& pos, int& n
       const uint32_t e = lut[st | byte];
       const int cn = c + (int)((e >> 8) & 15u);
       if (cn >= N) {
-        uint32_t q = pos + used;
-        if (!parse_tokens_serial(br, q, c, W, st != 0)) return false;
-        pos = q;
-        n = c;
+        // coefficient N - 1 is the byte's coefficient bit k; its 1 ends the
+        // part, with no closing test bit.  Bits used through it: k + 1
+        // coefficient bits and the test bits before them (the byte's first bit
+        // in the test state, and one after each earlier 1).
+        const uint32_t out = e & 0xffu;
+        const int k = N - 1 - c;
+        if (!((out >> k) & 1u)) return false;  // a run past the last coefficient
+        W |= (uint64_t)(out & ((2u << k) - 1u)) << c;
+        pos += used + (uint32_t)(k + 1) + (st ? 0u : 1u) + (uint32_t)__popc(out & ((1u << k) - 1u));
+        n = N;
         return true;
       }
       W |= (uint64_t)(e & 0xffu) << c;
