@@ -52,7 +52,7 @@ struct BlockMeta {
   uint64_t off;   // first bit of the brick in the component's payload
   int16_t s;      // scale exponent (R6), within [-1100, 1100]
   uint16_t len;   // bits of the block from the index; 0: nothing to parse (header final)
-  int8_t p;       // lowest coded plane, 0..64
+  int8_t p;       // lowest coded plane, 0..64 (64 when the block is not CODED)
   int8_t top;     // highest non-empty plane, -1 if none
   int8_t mode;
   uint8_t comp;   // component within the round
@@ -181,27 +181,28 @@ __device__ __forceinline__ bool parse_group(BlockBits& br, uint32_t& pos, int& n
       if (w == 2 && j == 1) return false;  // more than 17 bytes: malformed
       const uint32_t byte = ((j < 4 ? glo : ghi) >> (8 * (j & 3))) & 0xffu;
       const uint32_t e = lut[st | byte];
+      const uint32_t out = e & 0xffu;
       const int cn = c + (int)((e >> 8) & 15u);
-      if (cn >= N) {
-        // coefficient N - 1 is the byte's coefficient bit k; its 1 ends the
-        // part, with no closing test bit.  Bits used through it: k + 1
-        // coefficient bits and the test bits before them (the byte's first bit
-        // in the test state, and one after each earlier 1).
-        const uint32_t out = e & 0xffu;
-        const int k = N - 1 - c;
-        if (!((out >> k) & 1u)) return false;  // a run past the last coefficient
-        W |= (uint64_t)(out & ((2u << k) - 1u)) << c;
-        pos += used + (uint32_t)(k + 1) + (st ? 0u : 1u) + (uint32_t)__popc(out & ((1u << k) - 1u));
-        n = N;
+      if (cn >= N || (e & kTokEnded)) {  // the part ends in this byte
+        if (cn >= N) {
+          // coefficient N - 1 is the byte's coefficient bit k; its 1 ends the
+          // part, with no closing test bit.  Bits used through it: k + 1
+          // coefficient bits and the test bits before them (the byte's first
+          // bit in the test state, and one after each earlier 1).
+          const int k = N - 1 - c;
+          if (!((out >> k) & 1u)) return false;  // a run past the last coefficient
+          W |= (uint64_t)(out & ((2u << k) - 1u)) << c;
+          pos += used + (uint32_t)(k + 1) + (st ? 0u : 1u) + (uint32_t)__popc(out & ((1u << k) - 1u));
+          n = N;
+        } else {
+          W |= (uint64_t)out << c;
+          pos += used + ((e >> 13) & 7u) + 1;
+          n = cn;
+        }
         return true;
       }
-      W |= (uint64_t)(e & 0xffu) << c;
+      W |= (uint64_t)out << c;
       c = cn;
-      if (e & kTokEnded) {
-        pos += used + ((e >> 13) & 7u) + 1;
-        n = c;
-        return true;
-      }
       st = (e >> 5) & 0x100u;
       used += 8;
     }
@@ -229,6 +230,7 @@ __device__ bool parse_planes(BlockBits& br, uint32_t pos, uint32_t end, int p, u
     const int skip = min(z, pl - p + 1);
     pos += (uint32_t)skip;
     pl -= skip;
+    if (skip == z && z < 64) break;  // the bit after the zeros is the first significant plane's test 1
   }
   for (; pl >= p; --pl) {
     uint64_t W = 0;
@@ -342,21 +344,21 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
   if (cA || cB) {
     // lane l fetches plane l (and l + 32) of both bricks; planes outside
     // [p, top] are zero
-    auto fetch = [&](const BlockMeta& mX, bool cX, const uint64_t* sX, const uint64_t* pX, int pl) {
-      if (!cX || pl < mX.p || pl > mX.top) return (uint64_t)0;
+    auto fetch = [&](const BlockMeta& mX, const uint64_t* sX, const uint64_t* pX, int pl) {
+      if (pl < mX.p || pl > mX.top) return (uint64_t)0;  // a block not CODED has p = 64, top = -1
       const int rel = mX.top - pl;
       if (rel < Slots<T>::n) return sX[rel];
       return PCZ_CHECK(rel - Slots<T>::n < spill_per_block<T>(), 3) ? pX[rel - Slots<T>::n] : (uint64_t)0;
     };
-    const int lo = min(cA ? (int)mA.p : 64, cB ? (int)mB.p : 64);
-    const int hi = max(cA ? (int)mA.top : -1, cB ? (int)mB.top : -1);
+    const int lo = min((int)mA.p, (int)mB.p);
+    const int hi = max((int)mA.top, (int)mB.top);
     U u[4];
     if (hi - lo < 16) {
       // every coded plane of the pair lies in [lo, lo + 16): one transpose
       // carries two coefficient groups, rows 0-15 the planes of group 2t and
       // rows 16-31 those of group 2t + 1 (lane l fetches plane lo + (l & 15))
       const int pl = lo + (lane & 15);
-      const uint64_t WA = fetch(mA, cA, sA, pA, pl), WB = fetch(mB, cB, sB, pB, pl);
+      const uint64_t WA = fetch(mA, sA, pA, pl), WB = fetch(mB, sB, pB, pl);
       const uint32_t sel = h ? 0x7632u : 0x5410u;  // 16-bit group 2 t2 + h of both words
 #pragma unroll
       for (int t2 = 0; t2 < 2; ++t2) {
@@ -376,7 +378,7 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
           two = false;
         }
       }
-      const uint64_t WA0 = fetch(mA, cA, sA, pA, base + lane), WB0 = fetch(mB, cB, sB, pB, base + lane);
+      const uint64_t WA0 = fetch(mA, sA, pA, base + lane), WB0 = fetch(mB, sB, pB, base + lane);
       {
         uint32_t tl[4];
         tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
@@ -388,7 +390,7 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
       }
       if constexpr (WIDE) {
         if (two) {
-          const uint64_t WA1 = fetch(mA, cA, sA, pA, lane + 32), WB1 = fetch(mB, cB, sB, pB, lane + 32);
+          const uint64_t WA1 = fetch(mA, sA, pA, lane + 32), WB1 = fetch(mB, sB, pB, lane + 32);
           uint32_t th[4];
           th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
           th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
@@ -474,7 +476,7 @@ __device__ __forceinline__ void parse_task(const BoxJob& J, unsigned int* err, i
   BlockMeta bm = in;
   bm.mode = (int8_t)mode;
   bm.s = (int16_t)s;
-  bm.p = (int8_t)p;
+  bm.p = (int8_t)(mode == kModeCoded ? p : 64);  // no plane of a ZERO or RAW block is coded
   bm.top = (int8_t)top;
   meta[L] = bm;
 }
@@ -511,7 +513,7 @@ __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, 
     bm.off = 0;
     bm.s = 0;
     bm.len = 0;
-    bm.p = 0;
+    bm.p = 64;
     bm.top = -1;
     bm.mode = kModeZero;
     bm.comp = (uint8_t)jj;
