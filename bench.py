@@ -52,14 +52,14 @@ N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
 # capture of the current kernels (profiles/retrieve3_compress3_320cube_sections.md).
-TRAFFIC = {"retrieve": 1143408886}
+TRAFFIC = {"retrieve": 1140515275}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 16 retrieval launches of "
                   "the 320^3 case, scaled by the bricks processed to 512^3")
 # Pipe utilisation of the retrieval kernel (ncu --set full, k = 8 launch of the 320^3 case of
 # this workload, current kernels): it is bound by integer issue, not by HBM.
 PIPES = {"kernel": "retrieve", "launch": "k = 8, 320^3",
-         "alu": {"f32": 0.597, "f64": 0.613}, "fp64": {"f32": 0.0, "f64": 0.596},
-         "issue_active": {"f32": 0.650, "f64": 0.616},
+         "alu": {"f32": 0.570, "f64": 0.574}, "fp64": {"f32": 0.0, "f64": 0.662},
+         "issue_active": {"f32": 0.678, "f64": 0.605},
          "source": "ncu sm__inst_executed_pipe_{alu,fp64}.avg.pct_of_peak_sustained_active, "
                    "smsp__issue_active.avg.pct_of_peak_sustained_active"}
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
