@@ -1,10 +1,10 @@
 // pcz_compress.cu -- fused construction kernel: Algorithm 1 (Magri & Lindstrom,
 // Sec. 4.1) for every 4x4x4 brick of a 3D field, all n components in one pass.
 //
-// Per brick and component i the kernel computes the residual e = x - x~_{i-1}
-// e = x - x~, codes it with the PCZ coder at tau_i (y_i = C(e, tau_i)),
-// reconstructs x_i = D(y_i) from the coded planes and adds it into
-// x~.  x and x~ never leave registers, so the field is read once.
+// Per brick and component i the kernel computes the residual e = x - x~_{i-1},
+// codes it with the PCZ coder at tau_i (y_i = C(e, tau_i)), reconstructs
+// x_i = D(y_i) from the coded planes and adds it into x~.  x and x~ never
+// leave registers, so the field is read once.
 //
 // Layout: one CTA per index chunk of 32 bricks (R15), 16 warps; a warp codes
 // two bricks, 16 lanes each; lane t of a brick holds the x-line y = t & 3,
@@ -13,13 +13,13 @@
 // buffer in shared memory.  Bit planes come from 32x32 bit transposes across
 // the warp, after which lane p owns plane p (and p + 32): each lane emits its
 // plane's verbatim bits (R11), with the significance count before the plane
-// and the plane's bit offset from suffix scans over lanes (planes are coded from the
-// top down); the lane holding a coefficient writes the bits of the token that
-// makes it significant, at positions that follow from the plane's offset,
-// its significance count and the coefficient's rank among the plane's new
-// coefficients.  The chunk's bits are assembled in shared memory and appended to
-// a scratch pool with one atomic per chunk; pcz_misc.cu then scans the chunk
-// sizes and packs the final streams.
+// and the plane's bit offset from suffix scans over lanes (planes are coded
+// from the top down); the lane holding a coefficient writes the bits of the
+// token that makes it significant, at positions that follow from the plane's
+// offset, its significance count and the coefficient's rank among the plane's
+// new coefficients.  The chunk's bits are assembled in shared memory and
+// appended to a scratch pool with one atomic per chunk; pcz_misc.cu then scans
+// the chunk sizes and packs the final streams.
 #include "pcz_chunk3.cuh"
 
 namespace pcz {

@@ -15,18 +15,20 @@
 // (Algorithm 2's partial sums are the same whichever way they are reached).
 //
 // Layout: persistent CTAs of 8 warps, each taking units of 16 * umult
-// consecutive bricks of a job's box.  Components are handled in rounds of up to 8.  Parse
-// phase: warp w decodes the bit planes of component base + w for all 32
-// bricks of the unit, one brick per lane (plane parsing is sequential per
-// block, so this is where the lanes' parallelism comes from); a block's plane
-// words go to a shared-memory slot, counted from its top plane down, and the
-// few planes that do not fit to a per-CTA spill area in global memory.  After
-// a barrier, each warp rebuilds its 4 bricks two at a time (16 lanes per
-// brick, lane t holding the x-line y = t & 3, z = t >> 2): lane p fetches
-// plane p (and p + 32) of both bricks, a 32x32 bit transpose across the warp
-// turns planes back into each lane's coefficients t + 16j, and the inverse
-// reorder, lifting and scaling run through a bank-conflict-free brick buffer;
-// x_j is then added into x~, component by component in ascending order.
+// consecutive bricks of a job's box.  Components are handled in rounds of up
+// to 8.  Parse phase (parse_round): an index pass loads every task's block
+// position and length (a task is one block: one brick and component), a
+// counting sort orders the tasks longest first, and the warps steal them 32
+// at a time, one block per lane (plane parsing is sequential per block, so
+// this is where the lanes' parallelism comes from); a block's plane words go
+// to a shared-memory slot, counted from its top plane down, and the few
+// planes that do not fit to a per-CTA spill area in global memory.  After a
+// barrier, each warp rebuilds its brick pairs (16 lanes per brick, lane t
+// holding the x-line y = t & 3, z = t >> 2): lane p fetches plane p (and
+// p + 32) of both bricks, a 32x32 bit transpose across the warp turns planes
+// back into each lane's coefficients t + 16j, and the inverse reorder,
+// lifting and scaling run through a bank-conflict-free brick buffer; x_j is
+// then added into x~, component by component in ascending order.
 #include <type_traits>
 
 #include "pcz_device.cuh"
