@@ -627,6 +627,11 @@ def main():
         v, s, desc = oracle_sample(fields_np, args.sample, nthreads)
         cpu = {"value": round(v, 5), "unit": "GB/s", "cores": nthreads, "kind": "oracle", "sample": desc,
                "seconds": round(s, 2)}
+        # the paper's own mode: one core, on a smaller corner of the same fields
+        sub1 = max(4, args.sample // 2)
+        v1, s1, desc1 = oracle_sample(fields_np, sub1, 1)
+        cpu["single_core"] = {"value": round(v1, 5), "unit": "GB/s", "cores": 1, "sample": desc1,
+                              "seconds": round(s1, 2)}
     if rank == 0:
         line = {
             "metric": METRIC,
