@@ -50,7 +50,70 @@ CASES = [
     ("pl1d_f32_bin4", lambda: S.powerlaw((1001,), seed=17, dtype=np.float32), "bin4", 6),
     ("tiny1d_3", lambda: np.array([1.0, 2.0, 7.0]), None, 3),
     ("thin2d_1x70_f32", lambda: S.powerlaw((1, 70), seed=18, dtype=np.float32), "bin4", 5),
+    # Eq. 1 enforcement (Sec. 4.3): every brick RAW (float32 noise, one component
+    # below what its block exponent can code)
+    ("raw_noise_f32_one", lambda: np.random.default_rng(31).uniform(-1, 1, size=(24, 20, 18)).astype(np.float32),
+     [2.0 ** -26], 1),
+    # RAW and CODED bricks side by side in one warp, and the violations that
+    # floating point leaves where x~_1 is far from small values of x
+    ("viol_f32_3d", lambda: _wide((21, 19, 18), 33, np.float32), [0.25, 2.0 ** -30], 2),
+    ("viol_f64_3d", lambda: _wide((21, 19, 18), 34, np.float64), [0.25, 2.0 ** -59], 2),
+    ("viol_f32_1d", lambda: _wide((2051,), 35, np.float32), [0.25, 2.0 ** -30], 2),
+    ("viol_f64_2d", lambda: _wide((37, 41), 36, np.float64), [0.25, 2.0 ** -59], 2),
+    # the top of the float range: reconstructions round to infinity, the coder
+    # escalates and stores some bricks RAW
+    ("top_f32_bin", lambda: _top(np.float32, 0.9999, (18, 17, 16)), "bin4", 6),
+    ("top_f32_dec", lambda: _top(np.float32, 0.999, (18, 17, 16)), "dec", 6),
+    ("top_f64_bin", lambda: _top(np.float64, 0.9, (18, 17, 16)), "bin4", 6),
+    ("top2d_f64_dec", lambda: _top(np.float64, 0.99, (45, 38)), "dec", 6),
+    ("top1d_f32_bin", lambda: _top(np.float32, 0.9999, (1003,)), "bin4", 6),
+    # scales where quantisation and dequantisation leave the normal-range fast
+    # paths: subnormal values, residuals near 2^-100 (float32) and near the top
+    ("scaled_f32_1e-40", lambda: _scaled(1e-40, np.float32), "dec", 8),
+    ("scaled_f32_1e-36", lambda: _scaled(1e-36, np.float32), "dec", 8),
+    ("scaled_f32_1e37", lambda: _scaled(1e37, np.float32), "dec", 8),
+    ("scaled_f64_1e-310", lambda: _scaled(1e-310, np.float64), "dec", 8),
+    ("scaled_f64_1e306", lambda: _scaled(1e306, np.float64), "dec", 8),
+    # 1D bricks that escalate (every third brick; stored inputs), mixed with random bricks
+    ("esc1d_f32", lambda: _esc1d(0, 257, 50)[0], lambda: _esc1d(0, 257, 50)[1], 2),
+    ("esc1d_f64", lambda: _esc1d(3, 257, 51)[0], lambda: _esc1d(3, 257, 51)[1], 2),
 ]
+
+
+def _wide(shape, seed, dtype):
+    """N(0, 1) values each scaled by 2^-U(0, 8)."""
+    rng = np.random.default_rng(seed)
+    return (rng.normal(size=shape) * 2.0 ** rng.uniform(-8, 0, size=shape)).astype(dtype)
+
+
+def _top(dtype, frac, shape, seed=7):
+    """magnitudes in [frac, 1] of the largest finite value, signs of a k^-5/3 field
+    (one-signed for float64, so that the range max - min stays finite)."""
+    base = S.powerlaw(shape, seed=seed, dtype=np.float64)
+    base = base / np.abs(base).max()
+    mag = (frac + (1 - frac) * np.abs(base)) * float(np.finfo(dtype).max)
+    return (mag if dtype == np.float64 else np.sign(base) * mag).astype(dtype)
+
+
+def _scaled(scale, dtype):
+    return (S.powerlaw((20, 18, 17), seed=4, dtype=np.float64) * scale).astype(dtype)
+
+
+def _esc1d(row, nbricks, seed):
+    """every third brick the stored escalating brick of tests/golden/escalation_1d.txt
+    (row `row`), the others random; a ragged tail of 3 values.  Returns (x, tau)."""
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "escalation_1d.txt")
+    rows = [[p.strip() for p in ln.split("|")] for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    dtn, hexes, taus = rows[row]
+    dtype = np.float32 if dtn == "f32" else np.float64
+    ints = np.array([int(h, 16) for h in hexes.split(",")], dtype=np.uint32 if dtype == np.float32 else np.uint64)
+    brick = ints.view(dtype)
+    rng = np.random.default_rng(seed)
+    parts = [brick if j % 3 == 0 else (rng.normal(size=4) * 2.0 ** rng.uniform(-3, 3, size=4)).astype(dtype)
+             for j in range(nbricks)]
+    return np.concatenate(parts + [brick[:3]]), [float.fromhex(t) for t in taus.split()]
 
 
 def _steps(shape, seed, dtype):
@@ -68,6 +131,10 @@ def _noise(shape, seed, dtype, spread):
 
 
 def _tau(x, kind, n):
+    if callable(kind):
+        return kind()
+    if isinstance(kind, list):
+        return kind
     if kind is None:
         return [1.0 / (i + 1) for i in range(n)]
     r = O.value_range(x)
@@ -82,7 +149,7 @@ def pair(request, P):
     x = np.ascontiguousarray(make())
     tau = _tau(x, kind, n)
     xd = torch.from_numpy(x).cuda()
-    if kind is not None:  # the product's own schedule from the device range is the oracle's, bit for bit
+    if isinstance(kind, str):  # the product's own schedule from the device range is the oracle's, bit for bit
         r = P.value_range(xd)
         gt = P.tau_binary(r, {"bin4": 4, "bin8": 8}[kind], n) if kind.startswith("bin") else P.tau_decade(r, n)
         assert gt == tau
@@ -102,7 +169,7 @@ def test_streams_bitwise(pair):
         assert np.array_equal(c["chunk_word"], ref.chunk_word(i)), f"chunk offsets of component {i + 1}"
         assert np.array_equal(c["payload"], ref.payload(i)), f"payload of component {i + 1}"
         assert c["counts"] == [int(v) for v in ref.stats(i)]
-        assert gpu.counts(i)[4] == 0  # Eq. 1 held everywhere
+        assert gpu.counts(i) == c["counts"]
 
 
 def test_retrieve_bitwise_and_eq1(pair):
@@ -111,9 +178,9 @@ def test_retrieve_bitwise_and_eq1(pair):
         got = gpu.retrieve(k=k).cpu().numpy()
         want = ref.retrieve(k)
         assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), f"k={k}"
-        if k:
-            err = float(np.max(np.abs(np.subtract(x, got, dtype=x.dtype))))
-            assert err <= tau[k - 1]
+        if k:  # Eq. 1, with the violations floating point leaves counted, not hidden
+            err = np.abs(np.subtract(x, got, dtype=x.dtype)).astype(np.float64)
+            assert int(np.sum(err > tau[k - 1])) == int(ref.stats(k - 1)[O.ST_VIOL])
 
 
 def test_refine_equals_one_shot(pair):
