@@ -51,7 +51,7 @@ sys.path.insert(0, ROOT)
 N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
-# capture of the current kernels (profiles/retrieve3_compress3_320cube_sections.md).
+# capture of the current kernels.
 TRAFFIC = {"retrieve": 1140515275}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 16 retrieval launches of "
                   "the 320^3 case, scaled by the bricks processed to 512^3")
@@ -199,8 +199,7 @@ def run_pcz(args, rank, world, device):
         for name, x in fields.items():
             if host:  # e2e: the field is in pinned host memory; the kernels read it in place
                 x = hbufs[name]
-            lo, hi = pcz.field_range(x)  # a1: tau_0 = range
-            tau = pcz.tau_decade(hi - lo, N_COMP)
+            tau = pcz.field_tau_schedule(x, "decade", N_COMP)  # a1: tau_0 = range, tau_i
             if name in held:
                 held.pop(name).close()
             st = pcz.compress(x, tau)  # a2..a9
@@ -391,7 +390,7 @@ def run_serving(args, device):
         x = S.powerlaw((size, size, size), seed=100 + f, dtype=np.float32, device=device)
         lo, hi = pcz.field_range(x)
         ranges.append(hi - lo)
-        streams.append(pcz.compress(x, pcz.tau_decade(hi - lo, N_COMP)))
+        streams.append(pcz.compress(x, pcz.field_tau_schedule(x, "decade", N_COMP)))
         del x
     torch.cuda.synchronize()
     qs, arr = serve_queries(args.serve_queries, nf, size, ranges)
@@ -447,8 +446,7 @@ def run_batched(args, device):
             fields.append(S.powerlaw(sh, seed=200 + j, dtype=np.float32, device=device).contiguous())
     taus = []
     for x in fields:
-        lo, hi = pcz.field_range(x)
-        taus.append(pcz.tau_decade(hi - lo, 6))
+        taus.append(pcz.field_tau_schedule(x, "decade", 6))
     torch.cuda.synchronize()
     raw = sum(x.numel() * 4 for x in fields)
     plan = pcz.Batch(shapes, np.float32, 6)

@@ -184,6 +184,43 @@ pc_status pc_field_range(const void *d_field, int64_t count, pc_dtype dtype, voi
                          double *vmax);
 
 /*
+ * Tolerance schedules (Sec. 5.1: tolerances are relative to tau_0, the range
+ * of the field values, and fall geometrically, tau_i = 2^(-Delta i) tau_0).
+ *   PC_TAU_BINARY: tau_i = tau_0 * 2^(-param * i), i = 1..n, param = Delta >= 1
+ *     (param * n <= 4096).  One rounding: exact unless the value is subnormal,
+ *     and 0 once it falls below the smallest subnormal.
+ *   PC_TAU_DECADE: tau_i = c_i * tau_0 rounded once, i = 1..n, with c_i the
+ *     double nearest 10^-(param + i - 1), param >= 0 (param + n - 1 <= 400).
+ * pc_tau_schedule writes tau[0..n-1] (host, n in 1..PC_MAX_COMPONENTS) from a
+ * given tau_0 (positive, finite); pure host arithmetic, no GPU work.
+ * pc_field_tau_schedule first reduces the field's range on the device (as
+ * pc_field_range; device or pinned host memory, count values of dtype) and
+ * takes tau_0 = max - min rounded once in double; PC_ERR_ARG for a constant
+ * field (range 0) or a range that overflows.  It synchronises cuda_stream.
+ * A schedule that underflows to 0 is returned as computed; pc_compress
+ * rejects it with PC_ERR_TAU_ORDER.
+ */
+typedef enum { PC_TAU_BINARY = 1, PC_TAU_DECADE = 2 } pc_tau_kind;
+pc_status pc_tau_schedule(pc_tau_kind kind, double tau0, int param, int n, double *tau);
+pc_status pc_field_tau_schedule(const void *field, int64_t count, pc_dtype dtype, pc_tau_kind kind, int param, int n,
+                                void *cuda_stream, double *tau);
+
+/*
+ * Lossless sweep (Sec. 5.1.3: components are added until x~ reproduces x).
+ * Compresses the field (as pc_compress) with the binary schedule tau_i =
+ * 2^(-delta i) tau_0, i = 1..n_max (1 <= delta <= 64, n_max <= 64), stopping
+ * the schedule where it would underflow to 0; tau_0 is the field's range, or
+ * max(|value|, 1) for a constant field.  *out receives the streams (free with
+ * pc_streams_free), *k the first component whose computed tolerance
+ * (pc_stream_measured_error) is 0, i.e. whose x~_k equals x value for value
+ * (0 when none of them does), and *bits_per_value the stream bits of
+ * components 1..k, payload and index, per field value (0 when *k is 0).
+ * Errors as pc_compress.  Synchronises cuda_stream.
+ */
+pc_status pc_lossless_sweep(const void *field, const int64_t *dims, int ndims, pc_dtype dtype, int delta, int n_max,
+                            void *cuda_stream, pc_streams **out, int *k, double *bits_per_value);
+
+/*
  * Kernel timing (instrumentation, off by default).  While enabled, every
  * kernel the library launches is bracketed by CUDA events recorded on the
  * stream it is launched on.  pc_timing_read synchronises the device and
@@ -209,7 +246,7 @@ pc_status pc_timing_read(double *ms, uint64_t *launches);
  * memory (a framework's caching allocator, an application memory pool), or a
  * latency-critical loop that must avoid cudaMalloc/cudaFree, which can
  * synchronise the device.  It computes exactly what pc_compress computes
- * (Algorithm 1, the same streams bit for bit) but takes all its temporary
+ * (the same streams as pc_compress, bit for bit) but takes all its temporary
  * memory from one fixed 64 MiB device array inside the library, held on every
  * GPU that loads the library until the process exits, and writes the streams
  * into buffers the caller provides:
@@ -223,10 +260,12 @@ pc_status pc_timing_read(double *ms, uint64_t *launches);
  *   h_words     host, n: payload words per component.
  *   h_counts    host, 5 * n: the counters of pc_stream_counts per component.
  * Limit: n * ceil(bricks / 32) must not exceed the bound given in the
- * PC_ERR_ARG message (about 2000 for float64 and 4000 for float32 fields, e.g.
- * a 64^3 field with up to 15 float64 components); larger inputs are rejected
- * before any GPU work, and so is a too small payload buffer (its message
- * gives the words needed).  The library-internal array is shared by all
+ * PC_ERR_ARG message (2026 for one float64 component, 4042 for one float32
+ * component, a little less for more components; e.g. a 64^3 field with up to
+ * 15 float64 components); larger inputs are rejected before any GPU work, and
+ * so is a too small payload buffer (its message gives the words needed).  The
+ * four buffers must be device memory (PC_ERR_ARG otherwise); the index
+ * buffers must hold the sizes stated above.  The library-internal array is shared by all
  * calls: calls whose work overlaps on the GPU (other streams or threads) race
  * on it, so the caller must serialise them.  The first call on a device looks
  * up the array's device address; make that first call before any stream

@@ -96,6 +96,9 @@ def lib():
             "pc_server_replay": [vp, C.POINTER(Query), dp, C.c_int, C.POINTER(vp), dp, C.POINTER(ServeStats)],
             "pc_server_reset_cache": [vp],
             "pc_server_free": [vp],
+            "pc_tau_schedule": [C.c_int, C.c_double, C.c_int, C.c_int, dp],
+            "pc_field_tau_schedule": [vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, vp, dp],
+            "pc_lossless_sweep": [vp, i64p, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.POINTER(vp), ip, dp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -470,43 +473,58 @@ def field_range(x, stream=None):
 
 # ---- tolerance schedules (Sec. 5.1: tau_i = 2^(-delta i) tau_0, tau_0 = range) ----
 
-def value_range(x, stream=None) -> float:
-    lo, hi = field_range(x, stream)
-    return hi - lo
+PC_TAU_BINARY, PC_TAU_DECADE = 1, 2
 
 
-def tau_binary(rng: float, delta: int, n: int):
-    """tau_i = 2^(-delta * i) * tau_0 for i = 1..n."""
-    return [rng * 2.0 ** (-delta * i) for i in range(1, n + 1)]
+def _schedule(kind, tau0, param, n):
+    out = (C.c_double * n)()
+    _check(lib().pc_tau_schedule(kind, float(tau0), int(param), int(n), out))
+    return list(out)
 
 
-def tau_decade(rng: float, n: int, first_exp: int = 2):
-    """tau_i = 10^-(first_exp + i - 1) * tau_0 for i = 1..n: each decimal factor
-    is the double nearest to it, times the range with one rounding."""
-    return [float("1e-%d" % (first_exp + i - 1)) * rng for i in range(1, n + 1)]
+def tau_binary(tau0: float, delta: int, n: int):
+    """tau_i = 2^(-delta * i) * tau_0 for i = 1..n (pc_tau_schedule)."""
+    return _schedule(PC_TAU_BINARY, tau0, delta, n)
+
+
+def tau_decade(tau0: float, n: int, first_exp: int = 2):
+    """tau_i = 10^-(first_exp + i - 1) * tau_0 for i = 1..n (pc_tau_schedule)."""
+    return _schedule(PC_TAU_DECADE, tau0, first_exp, n)
+
+
+def field_tau_schedule(x, kind: str, n: int, param=None, stream=None):
+    """The schedule of a CUDA tensor (or pinned host tensor) relative to its own
+    range, tau_0 = max - min reduced on the device (pc_field_tau_schedule):
+    kind "binary" (param = delta, default 4) or "decade" (param = first
+    exponent, default 2)."""
+    code = {"binary": PC_TAU_BINARY, "decade": PC_TAU_DECADE}[kind]
+    if param is None:
+        param = 4 if kind == "binary" else 2
+    out = (C.c_double * n)()
+    _check(lib().pc_field_tau_schedule(_ptr(x), x.numel(), _dtype_code(x.dtype), code, int(param), int(n),
+                                       _stream_ptr(stream), out))
+    return list(out)
 
 
 def lossless_sweep(x, delta: int = 4, n_max: int = 64, stream=None):
-    """Sec. 5.1.3: components are added until x~ reproduces x.  Compresses x
-    with the binary schedule tau_i = 2^(-delta i) * range, i = 1..n_max, and
-    returns dict(k = the first component whose computed tolerance is 0 (None
-    if none), bits_per_value = stream bits of components 1..k including their
-    index, ratio = bits of the type / bits_per_value, measured = the computed
-    tolerances).  The streams object is returned under "streams"."""
-    rng = value_range(x, stream)
-    if rng == 0.0:
-        rng = max(abs(field_range(x, stream)[0]), 1.0)
-    tau = [t for t in tau_binary(rng, delta, n_max) if t > 0.0]
-    st = compress(x, tau, stream)
+    """Sec. 5.1.3 (pc_lossless_sweep): components are added until x~ reproduces
+    x, with the binary schedule tau_i = 2^(-delta i) * range.  Returns dict(k =
+    the first component whose computed tolerance is 0 (None if none),
+    bits_per_value = stream bits of components 1..k including their index,
+    ratio = bits of the type / bits_per_value, measured = the computed
+    tolerances, streams = the Streams object)."""
+    dims = (C.c_int64 * 3)(*([int(v) for v in reversed(x.shape)] + [1] * (3 - x.dim())))
+    h = C.c_void_p()
+    k = C.c_int()
+    bpv = C.c_double()
+    _check(lib().pc_lossless_sweep(_ptr(x), dims, x.dim(), _dtype_code(x.dtype), int(delta), int(n_max),
+                                   _stream_ptr(stream), C.byref(h), C.byref(k), C.byref(bpv)))
+    st = Streams(h, tuple(x.shape), x.dtype)
     meas = [st.measured_error(i) for i in range(st.n)]
-    k = next((i + 1 for i, m in enumerate(meas) if m == 0.0), None)
-    nvals = int(np.prod(st.shape))
-    bits = None
-    if k is not None:
-        bits = sum(st.info(i)[1] + 8 * st.info(i)[2] for i in range(k)) / nvals
     tbits = 32 if st.dtype in (_torch().float32,) else 64
-    return {"k": k, "bits_per_value": bits, "ratio": (tbits / bits) if bits else None, "measured": meas,
-            "streams": st}
+    kk = k.value or None
+    return {"k": kk, "bits_per_value": bpv.value if kk else None, "ratio": (tbits / bpv.value) if kk else None,
+            "measured": meas, "streams": st}
 
 
 def debug_status(reset: bool = False):

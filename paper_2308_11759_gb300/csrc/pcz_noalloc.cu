@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pcz.h"
+#include "pcz_host.h"
 #include "pcz_kernels.h"
 
 using namespace pcz;
@@ -47,6 +48,34 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // Largest bit string one brick and component can take (a CODED block whose
 // every plane is non-empty), as in the compress kernel.
 int64_t max_brick_bits(pc_dtype dt) { return dt == PC_F32 ? 2 + 3 + 8 + 32 * 129 : 2 + 3 + 11 + 64 * 129; }
+
+// Pool words the worst chunk (32 such bricks) takes.
+uint64_t worst_chunk_words(pc_dtype dt) { return (uint64_t)((kChunk * max_brick_bits(dt) + 63) / 64); }
+
+// Byte offsets of the scratch regions for n components of nchunks chunks:
+// per (component, chunk) 32 bytes of metadata (word count, pool offset, five
+// counters), per component 56 bytes (total, counters, payload base), the
+// flags, and then the bit pool.
+struct Layout {
+  size_t nwords, cpool, ccnt, tot, cnt, flags, base, pool;
+};
+Layout layout(int n, int64_t nchunks) {
+  Layout l;
+  l.nwords = 0;
+  l.cpool = align256(l.nwords + 4 * (size_t)n * nchunks);
+  l.ccnt = align256(l.cpool + 8 * (size_t)n * nchunks);
+  l.tot = align256(l.ccnt + 20 * (size_t)n * nchunks);
+  l.cnt = align256(l.tot + 8 * (size_t)n);
+  l.flags = align256(l.cnt + 40 * (size_t)n);
+  l.base = align256(l.flags + 16);
+  l.pool = align256(l.base + 8 * (size_t)n);
+  return l;
+}
+// True when the worst case of every chunk of every component fits the pool.
+bool fits(const Layout& l, int n, int64_t nchunks, uint64_t chunk_worst_words) {
+  if (l.pool > kScratchBytes) return false;
+  return chunk_worst_words * (uint64_t)n * (uint64_t)nchunks <= (kScratchBytes - l.pool) / 8;
+}
 
 }  // namespace
 
@@ -76,21 +105,25 @@ pc_status pc_compress_noalloc(const void* d_field, const int64_t* dims, int ndim
   const int64_t nchunks = (nbricks + kChunk - 1) / kChunk;
 
   // scratch layout: per-chunk metadata, totals, flags, then the bit pool
-  const size_t off_nwords = 0;
-  const size_t off_cpool = align256(off_nwords + 4 * (size_t)n * nchunks);
-  const size_t off_ccnt = align256(off_cpool + 8 * (size_t)n * nchunks);
-  const size_t off_tot = align256(off_ccnt + 20 * (size_t)n * nchunks);
-  const size_t off_cnt = align256(off_tot + 8 * (size_t)n);
-  const size_t off_flags = align256(off_cnt + 40 * (size_t)n);
-  const size_t off_base = align256(off_flags + 16);
-  const size_t off_pool = align256(off_base + 8 * (size_t)n);
-  // the worst case every chunk of every component can take in the pool
-  const uint64_t chunk_worst_words = (uint64_t)((kChunk * max_brick_bits(dtype) + 63) / 64);
-  const uint64_t pool_worst_words = chunk_worst_words * (uint64_t)n * (uint64_t)nchunks;
-  if (off_pool > kScratchBytes || pool_worst_words > (kScratchBytes - off_pool) / 8)
-    return nfail(PC_ERR_ARG, "field too large for the fixed 64 MiB scratch of pc_compress_noalloc: need n * ceil(bricks/32) <= " +
-                                 std::to_string((kScratchBytes - off_pool) / 8 / chunk_worst_words) +
+  const Layout lay = layout(n, nchunks);
+  const uint64_t chunk_worst_words = worst_chunk_words(dtype);
+  if (!fits(lay, n, nchunks, chunk_worst_words)) {
+    // the largest n * ceil(bricks/32) that fits for this n, from the same layout
+    int64_t lo = 0, hi = (int64_t)(kScratchBytes / 8 / chunk_worst_words) + 1;  // fits(lo), !fits(hi)
+    while (hi - lo > 1) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (fits(layout(n, mid), n, mid, chunk_worst_words)) lo = mid; else hi = mid;
+    }
+    return nfail(PC_ERR_ARG, "field too large for the fixed 64 MiB scratch of pc_compress_noalloc: with n = " +
+                                 std::to_string(n) + " it needs n * ceil(bricks/32) <= " + std::to_string((int64_t)n * lo) +
                                  " (bricks are 4x4x4 values); use pc_compress");
+  }
+  // outputs and the field must be device memory the kernels can write/read
+  if (!device_pointer(d_field) || !device_pointer(d_payload) || !device_pointer(d_chunk_word) ||
+      !device_pointer(d_brick_len))
+    return nfail(PC_ERR_ARG, "d_field, d_payload, d_chunk_word and d_brick_len must be device memory");
+  const size_t off_nwords = lay.nwords, off_cpool = lay.cpool, off_ccnt = lay.ccnt, off_tot = lay.tot,
+               off_cnt = lay.cnt, off_flags = lay.flags, off_base = lay.base, off_pool = lay.pool;
 
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int dev = 0;

@@ -79,3 +79,32 @@ def test_argument_errors_without_device_work(L):
     buf = (C.c_ubyte * 16)()
     assert L.pc_streams_deserialize(buf, 16, None, C.byref(st)) == 8  # PC_ERR_VERSION: too short
     assert P.STATUS[8] == "PC_ERR_VERSION"
+
+
+def test_tau_schedules_on_the_host(L):
+    """pc_tau_schedule (pure host arithmetic, no GPU): each tolerance is the
+    exact schedule value rounded once to double (Sec. 5.1), checked with exact
+    rationals, and the values equal the oracle's own copy of the rule."""
+    from fractions import Fraction
+
+    import oracle as O
+    import paper_2308_11759_gb300 as P
+
+    for tau0 in (1.0, 3.7, 0.1234567, 2.5e-300, 1.7e308, 6.02e23):
+        for delta in (1, 4, 8, 16):
+            got = P.tau_binary(tau0, delta, 12)
+            assert got == O.tau_binary(tau0, delta, 12)
+            for i, t in enumerate(got, 1):
+                assert t == float(Fraction(tau0) / 2 ** (delta * i))
+        for first in (0, 1, 2, 7):
+            got = P.tau_decade(tau0, 10, first_exp=first)
+            assert got == O.tau_decade(tau0, 10, first_exp=first)
+            for i, t in enumerate(got, 1):
+                c = float(Fraction(1, 10 ** (first + i - 1)))  # the double nearest 10^-e
+                assert t == float(Fraction(c) * Fraction(tau0))
+    out = (C.c_double * 4)()
+    assert L.pc_tau_schedule(P.PC_TAU_BINARY, -1.0, 4, 4, out) == 1
+    assert L.pc_tau_schedule(P.PC_TAU_BINARY, float("inf"), 4, 4, out) == 1
+    assert L.pc_tau_schedule(P.PC_TAU_BINARY, 1.0, 0, 4, out) == 1
+    assert L.pc_tau_schedule(7, 1.0, 4, 4, out) == 1
+    assert L.pc_tau_schedule(P.PC_TAU_DECADE, 1.0, 2, 0, out) == 1

@@ -41,7 +41,7 @@ for shape, dt, n in cases:
 shapes = [(33, 20, 18), (90, 70), (300,)]
 plan = P.Batch(shapes, np.float32, 4)
 xs = [torch.from_numpy(np.ascontiguousarray(S.powerlaw(s, seed=6, dtype=np.float32))).cuda() for s in shapes]
-sts = plan.compress(xs, [P.tau_decade(P.value_range(x), 4) for x in xs])
+sts = plan.compress(xs, [P.field_tau_schedule(x, "decade", 4) for x in xs])
 P.retrieve_batch(sts, [4] * 3)
 srv = P.Server(4 << 30, max_batch=64)
 fid = srv.add_field(sts[0])

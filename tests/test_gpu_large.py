@@ -52,7 +52,7 @@ def test_512_full_streams(P, dt):
     del x64
     x = xd.cpu().numpy()
     tau = O.tau_decade(O.value_range(x), 8)
-    assert P.tau_decade(P.value_range(xd), 8) == tau
+    assert P.field_tau_schedule(xd, "decade", 8) == tau
     st = P.compress(xd, tau)
     ref = O.Streams(x, tau, nthreads=os.cpu_count() or 1)
     for i in range(8):
@@ -81,7 +81,7 @@ def test_1024_fronts_sampled(P):
     lo_v, hi_v = xd.min().item(), xd.max().item()
     rng_v = float(np.float64(hi_v) - np.float64(lo_v))
     tau = O.tau_decade(rng_v, n, first_exp=1)  # tau_i = 10^-i * range, i = 1..12
-    assert P.tau_decade(P.value_range(xd), n, first_exp=1) == tau
+    assert P.field_tau_schedule(xd, "decade", n, param=1) == tau
     st = P.compress(xd, tau)
     for i in range(n):
         assert st.counts(i)[4] == 0

@@ -150,8 +150,10 @@ def pair(request, P):
     tau = _tau(x, kind, n)
     xd = torch.from_numpy(x).cuda()
     if isinstance(kind, str):  # the product's own schedule from the device range is the oracle's, bit for bit
-        r = P.value_range(xd)
-        gt = P.tau_binary(r, {"bin4": 4, "bin8": 8}[kind], n) if kind.startswith("bin") else P.tau_decade(r, n)
+        if kind.startswith("bin"):
+            gt = P.field_tau_schedule(xd, "binary", n, param={"bin4": 4, "bin8": 8}[kind])
+        else:
+            gt = P.field_tau_schedule(xd, "decade", n)
         assert gt == tau
     gpu = P.compress(xd, tau)
     ref = O.Streams(x, tau, nthreads=4)

@@ -87,6 +87,73 @@ def test_noalloc_equals_pc_compress_on_consecutive_calls(P):
     _check_same_as_pc_compress(P, a, _tau(a, "bin4", 4))
 
 
+def test_noalloc_allocates_no_device_memory(P):
+    # after a first call (which looks up the library array's address), a second
+    # call of the same size leaves the device's free memory exactly as it was
+    x = S.gaussians((48, 40, 36), seed=4)
+    xd = torch.from_numpy(x).cuda()
+    tau = _tau(x, "bin4", 4)
+    shape = tuple(xd.shape)
+    nb = [(d + 3) // 4 for d in shape[::-1]]
+    nbricks = nb[0] * nb[1] * nb[2]
+    nchunks = (nbricks + 31) // 32
+    cap = 4 * nbricks * 140 + 64
+    payload = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    chunk_word = torch.zeros(4 * nchunks, dtype=torch.int64, device="cuda")
+    brick_len = torch.zeros(4 * nbricks, dtype=torch.int16, device="cuda")
+    words = (C.c_uint64 * 4)()
+    counts = (C.c_uint64 * 20)()
+    taus = (C.c_double * 4)(*tau)
+    dims = (C.c_int64 * 3)(*shape[::-1])
+
+    def call():
+        rc = P.lib().pc_compress_noalloc(xd.data_ptr(), dims, 3, P.PC_F64, taus, 4, payload.data_ptr(), cap,
+                                         chunk_word.data_ptr(), brick_len.data_ptr(), words, counts,
+                                         torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        return rc
+
+    assert call() == 0
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    assert call() == 0
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_reserved() == reserved0
+
+
+def test_noalloc_size_bound_is_exact(P):
+    # the bound the refusal states is accepted, one chunk more is refused
+    xd = torch.zeros(8, device="cuda", dtype=torch.float64)
+    dims = (C.c_int64 * 3)(1024, 1024, 1024)
+    words = (C.c_uint64 * 1)()
+    counts = (C.c_uint64 * 5)()
+    taus = (C.c_double * 1)(0.5)
+    rc = P.lib().pc_compress_noalloc(xd.data_ptr(), dims, 3, P.PC_F64, taus, 1, xd.data_ptr(), 1, xd.data_ptr(),
+                                     xd.data_ptr(), words, counts, None)
+    msg = P.lib().pc_last_error().decode()
+    assert rc == 1
+    bound = int(msg.split("<=")[1].split()[0])  # chunks of one component
+    assert 2000 <= bound <= 2100
+    x = S.powerlaw((4, 4, 4 * 32 * bound), seed=6, dtype=np.float64)  # exactly `bound` chunks
+    _check_same_as_pc_compress(P, x, [0.5])
+    dims = (C.c_int64 * 3)(4 * 32 * (bound + 1), 4, 4)
+    rc = P.lib().pc_compress_noalloc(xd.data_ptr(), dims, 3, P.PC_F64, taus, 1, xd.data_ptr(), 1, xd.data_ptr(),
+                                     xd.data_ptr(), words, counts, None)
+    assert rc == 1 and "scratch" in P.lib().pc_last_error().decode()
+
+
+def test_noalloc_refuses_host_pointers(P):
+    x = np.zeros((8, 8, 8))
+    dims = (C.c_int64 * 3)(8, 8, 8)
+    words = (C.c_uint64 * 1)()
+    counts = (C.c_uint64 * 5)()
+    taus = (C.c_double * 1)(0.5)
+    d = torch.zeros(1024, device="cuda", dtype=torch.int64)
+    rc = P.lib().pc_compress_noalloc(x.ctypes.data, dims, 3, P.PC_F64, taus, 1, d.data_ptr(), 1024, d.data_ptr(),
+                                     d.data_ptr(), words, counts, None)
+    assert rc == 1 and b"device memory" in P.lib().pc_last_error()
+
+
 def test_noalloc_refuses_inputs_beyond_its_scratch(P):
     xd = torch.zeros(8, device="cuda", dtype=torch.float64)
     dims = (C.c_int64 * 3)(256, 256, 256)  # 262144 bricks: beyond the fixed scratch
