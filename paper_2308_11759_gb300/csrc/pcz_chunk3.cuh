@@ -106,6 +106,9 @@ __device__ __forceinline__ void plane_scan2(uint64_t WA, bool actA, uint64_t WB,
   csum += __shfl_sync(FULL, sum, 0);
 }
 
+// Byte m of a register of four packed shared-memory slots.
+__device__ __forceinline__ int slot_of(uint32_t packed, int m) { return (int)((packed >> (8 * m)) & 0xffu); }
+
 // Algorithm 1 on every brick of index chunk `chunk` of a 3D field, all
 // components, by the whole CTA (kCompressThreads3 threads); smem holds
 // compress_smem3<T>() bytes.  Every thread of the CTA must call it.
@@ -207,19 +210,18 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     e[m] = F::sub(x[m], T(0));
   }
   S* buf = bbuf + warp * 128;
-  // buffer slots of this lane's line in each pass and of its coded coefficients
+  // buffer slots (each below 128) of this lane's line in each pass and of its
+  // coded coefficients, four to a register: slot m of a pass is byte m
   const int xx = t & 3, yq = t >> 2;
-  int ix[4], iy[4], iz[4], ir[4];
+  uint32_t pix = 0u, piy = 0u, piz = 0u, pir = 0u;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    ix[m] = sidx<T>(m, ly, lz, h);   // x-line of (y = ly, z = lz)
-    iy[m] = sidx<T>(xx, m, yq, h);   // y-line of (x = xx, z = yq)
-    iz[m] = sidx<T>(xx, yq, m, h);   // z-line of (x = xx, y = yq)
+    pix |= (uint32_t)sidx<T>(m, ly, lz, h) << (8 * m);   // x-line of (y = ly, z = lz)
+    piy |= (uint32_t)sidx<T>(xx, m, yq, h) << (8 * m);   // y-line of (x = xx, z = yq)
+    piz |= (uint32_t)sidx<T>(xx, yq, m, h) << (8 * m);   // z-line of (x = xx, y = yq)
     const int pos = kPerm3.pos[t + 16 * m];
-    ir[m] = sidx<T>(pos & 3, (pos >> 2) & 3, pos >> 4, h);
+    pir |= (uint32_t)sidx<T>(pos & 3, (pos >> 2) & 3, pos >> 4, h) << (8 * m);
   }
-  uint32_t tkeep[5];
-  transpose_masks(lane, tkeep);
   unsigned long long pool_base = 0;  // thread 0 only
   unsigned pool_nw = 0;
 
@@ -278,58 +280,58 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     // R7: lifting along x (in the lane), y and z (shared buffer)
     lift_fwd(q[0], q[1], q[2], q[3]);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) buf[ix[m]] = q[m];
+    for (int m = 0; m < 4; ++m) buf[slot_of(pix, m)] = q[m];
     __syncwarp();
     {
-      S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
+      S a = buf[slot_of(piy, 0)], bq = buf[slot_of(piy, 1)], c = buf[slot_of(piy, 2)], d = buf[slot_of(piy, 3)];
       lift_fwd(a, bq, c, d);
-      buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
+      buf[slot_of(piy, 0)] = a; buf[slot_of(piy, 1)] = bq; buf[slot_of(piy, 2)] = c; buf[slot_of(piy, 3)] = d;
     }
     __syncwarp();
     {
-      S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
+      S a = buf[slot_of(piz, 0)], bq = buf[slot_of(piz, 1)], c = buf[slot_of(piz, 2)], d = buf[slot_of(piz, 3)];
       lift_fwd(a, bq, c, d);
-      buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
+      buf[slot_of(piz, 0)] = a; buf[slot_of(piz, 1)] = bq; buf[slot_of(piz, 2)] = c; buf[slot_of(piz, 3)] = d;
     }
     __syncwarp();
     // R8, R9: coded order, negabinary.  Lane t holds coefficients t + 16j.
     U u[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) u[j] = nb_fwd<T>(buf[ir[j]]);
+    for (int j = 0; j < 4; ++j) u[j] = nb_fwd<T>(buf[slot_of(pir, j)]);
     __syncwarp();
 
     // R10, R13: lowest coded plane; lowered until Eq. 1 holds in T
     const int L = P.L[i];
     int esc = 0, p = 0;
     bool done = zero_blk || raw_forced, pass = false;
-    T xtc[4], ec[4];
+    // x~ + x_i of the passing precision; the carried residual e takes its
+    // x - (x~ + x_i) at the same time (a RAW brick recomputes the residual it
+    // stores from x - x~, which is the same value)
+    T xtc[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      xtc[m] = xt[m];
-      ec[m] = e[m];
-    }
+    for (int m = 0; m < 4; ++m) xtc[m] = xt[m];
     for (int round = 0; round < 8; ++round) {  // esc runs 0..7: at most 8 rounds
       const bool active = !done;
       const int pp = min(max(L + s - C - esc, 0), F::P);
       const U keep = pp >= F::P ? U(0) : (U)~((U(1) << pp) - 1);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>((U)(u[j] & keep));
+      for (int j = 0; j < 4; ++j) buf[slot_of(pir, j)] = nb_inv<T>((U)(u[j] & keep));
       __syncwarp();
       {
-        S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
+        S a = buf[slot_of(piz, 0)], bq = buf[slot_of(piz, 1)], c = buf[slot_of(piz, 2)], d = buf[slot_of(piz, 3)];
         lift_inv(a, bq, c, d);
-        buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
+        buf[slot_of(piz, 0)] = a; buf[slot_of(piz, 1)] = bq; buf[slot_of(piz, 2)] = c; buf[slot_of(piz, 3)] = d;
       }
       __syncwarp();
       {
-        S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
+        S a = buf[slot_of(piy, 0)], bq = buf[slot_of(piy, 1)], c = buf[slot_of(piy, 2)], d = buf[slot_of(piy, 3)];
         lift_inv(a, bq, c, d);
-        buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
+        buf[slot_of(piy, 0)] = a; buf[slot_of(piy, 1)] = bq; buf[slot_of(piy, 2)] = c; buf[slot_of(piy, 3)] = d;
       }
       __syncwarp();
       S r[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
+      for (int m = 0; m < 4; ++m) r[m] = buf[slot_of(pix, m)];
       __syncwarp();
       lift_inv(r[0], r[1], r[2], r[3]);
       bool ok = true;
@@ -362,7 +364,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
             xtc[m] = xtn[m];
-            ec[m] = en[m];
+            e[m] = en[m];
           }
         } else if (esc == 7 || pp == 0) {
           done = true;
@@ -377,6 +379,8 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     // lane l then holds plane l (and l + 32) of both bricks.
     uint64_t WA0, WB0, WA1 = 0, WB1 = 0;
     {
+      uint32_t tkeep[5];
+      transpose_masks(lane, tkeep);
       uint32_t tl[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) tl[j] = transpose32((uint32_t)u[j], lane, tkeep);
@@ -424,13 +428,30 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       }
     }
 
+    // the residual x - x~_{i-1} again, padded (R4), where a brick may be RAW:
+    // the value the coder started from, which the loop above has replaced
+    // by the next residual in passing bricks
+    T eo[4];
+    const bool need_eo = __any_sync(FULL, !zero_blk && (!pass || lenC > LEN_RAW));
+    if (need_eo) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) eo[m] = F::sub(x[m], xt[m]);
+      if (any_partial) {
+        const T last = nvx == 1 ? eo[0] : nvx == 2 ? eo[1] : nvx == 3 ? eo[2] : eo[3];
+#pragma unroll
+        for (int m = 1; m < 4; ++m)
+          if (m >= nvx) eo[m] = last;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) eo[m] = __shfl_sync(FULL, eo[m], srcl);
+      }
+    }
     // R14: RAW replaces a longer CODED brick only if it also meets tau_i
     bool raw_ok = false;
     if (__any_sync(FULL, pass && lenC > LEN_RAW)) {
       bool ok = true;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const T a = F::add(xt[m], e[m]);
+        const T a = F::add(xt[m], eo[m]);
         if (line_in && m < nvx && !within<T>(F::sub(x[m], a), tb)) ok = false;
       }
       raw_ok = (__ballot_sync(FULL, !ok) & HALF) == 0u;
@@ -438,26 +459,24 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     const int mode = zero_blk ? kModeZero : (pass && !(lenC > LEN_RAW && raw_ok)) ? kModeCoded : kModeRaw;
     const int blen = !have ? 0 : mode == kModeZero ? 2 : mode == kModeRaw ? LEN_RAW : lenC;
 
-    // x~_i and the next residual, committed after the bits are written
-    // (a RAW brick stores the current residual)
-    T xtnew[4], enew[4];
+    // x~_i and the next residual (a RAW brick stores the residual it started
+    // from); the next residual is in e already for CODED and ZERO bricks
     int viol = 0;  // Eq. 1 failures left (only a RAW brick can have them)
     U merr = 0;    // max |x - x~_i| over this lane's in-field values, as bits (Sec. 4.3)
+    if (need_eo) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (mode == kModeRaw) {
+          xtc[m] = F::add(xt[m], eo[m]);
+          e[m] = F::sub(x[m], xtc[m]);
+        }
+      }
+    }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      if (mode == kModeCoded) {
-        xtnew[m] = xtc[m];
-        enew[m] = ec[m];
-      } else if (mode == kModeRaw) {
-        xtnew[m] = F::add(xt[m], e[m]);
-        enew[m] = F::sub(x[m], xtnew[m]);
-      } else {
-        xtnew[m] = xt[m];
-        enew[m] = e[m];
-      }
       if (line_in && m < nvx) {
-        if (!within<T>(enew[m], tb)) ++viol;
-        const U a = F::bits(enew[m]) & F::ABS;
+        if (!within<T>(e[m], tb)) ++viol;
+        const U a = F::bits(e[m]) & F::ABS;
         merr = a > merr ? a : merr;
       }
     }
@@ -537,7 +556,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     if (have && mode == kModeRaw) {
       if (t == 0) or_bits_in(cbuf, boff, (uint64_t)kModeRaw, CAP, 0);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) or_bits_in(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(e[m]), CAP, 0);
+      for (int m = 0; m < 4; ++m) or_bits_in(cbuf, boff + 2 + F::P * (4 * t + m), (uint64_t)F::bits(eo[m]), CAP, 0);
     } else if (have && mode == kModeCoded && t == 0) {
       or_bits_in(cbuf, boff, (uint64_t)kModeCoded | ((uint64_t)esc << 2) | ((uint64_t)(emax + F::EBIAS) << 5), CAP,
                  0);
@@ -572,10 +591,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       }
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      xt[m] = xtnew[m];
-      e[m] = enew[m];
-    }
+    for (int m = 0; m < 4; ++m) xt[m] = xtc[m];
     if (tid == 0) {
       unsigned long long base = pool_base;
       if (base + pool_nw > P.pool_words) {

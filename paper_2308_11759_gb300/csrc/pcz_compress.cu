@@ -25,7 +25,7 @@
 namespace pcz {
 
 template <typename T>
-__global__ void __launch_bounds__(kCompressThreads3, 1) k_compress3(const CompressParams P) {
+__global__ void __launch_bounds__(kCompressThreads3, 2) k_compress3(const CompressParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   compress3_chunk<T>(P, (int64_t)blockIdx.x, smem);
 }
