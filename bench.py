@@ -269,6 +269,31 @@ def run_pcz(args, rank, world, device):
                           "gbs_algorithmic": round(alg[k] / (ms * 1e-3) / 1e9, 1) if k in alg and ms > 0 else None}
     launches = sum(n for _, n in ktimes.values())
 
+    # per field type: kernel times of one more step, from the library's events
+    per_dtype = {}
+    for name, x in fields.items():
+        st = held[name]
+        fb = info[name]["field_bytes"]
+        tau = [st.tau(i) for i in range(st.n)]
+        pcz.timing_enable(True)
+        st2 = pcz.compress(x, tau)
+        tc = pcz.timing_read()
+        rms = []
+        for k in range(1, N_COMP + 1):
+            pcz.timing_enable(True)
+            st2.retrieve(k=k, out=outs[name])
+            tr = pcz.timing_read()
+            rms.append(tr["retrieve"][0])
+        pcz.timing_enable(False)
+        st2.close()
+        cms = tc["compress"][0]
+        per_dtype[name] = {"compress_ms": round(cms, 3), "compress_gbs": round(fb / (cms * 1e-3) / 1e9, 2),
+                           "compress_roofline_frac": round(info[name]["compress_bytes"] / (cms * 1e-3) / 1e9 / hbm, 5),
+                           "retrieve_ms_per_k": [round(v, 3) for v in rms],
+                           "retrieve_gbs": round(N_COMP * fb / (sum(rms) * 1e-3) / 1e9, 2),
+                           "retrieve_roofline_frac": round(sum(info[name]["retrieve_bytes"]) / (sum(rms) * 1e-3) / 1e9
+                                                           / hbm, 5)}
+
     # accuracy gain (Sec. 5.1.1): alpha_k = log2(sigma / RMSE_k) - R_k, with R_k the
     # stream bits per value of components 1..k (index included)
     gain = {}
@@ -346,6 +371,7 @@ def run_pcz(args, rank, world, device):
     for st in held.values():
         st.close()
     return dict(value=value, ms_step=ms_step, info=info, clocks=clocks, kernels=kernels, launches=launches, gain=gain,
+                per_dtype=per_dtype,
                 sweep=sweep,
                 roofline={"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
                           "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -491,6 +517,24 @@ def run_batched(args, device):
         st.close()
     info = plan.info()
     plan.close()
+    # the oracle on a sample of the batch: a 512^2 corner of the first 2D field
+    # and a 64^3 corner of the first 3D field, compress + retrieval at k = 6
+    import oracle as O
+
+    sample = [np.ascontiguousarray(fields[0][:512, :512].cpu().numpy()),
+              np.ascontiguousarray(fields[1][:64, :64, :64].cpu().numpy())]
+    oracle = {}
+    for cores in (1, os.cpu_count() or 1):
+        t = time.perf_counter()
+        for xs in sample:
+            tau = O.tau_decade(O.value_range(xs), 6)
+            O.Streams(xs, tau, nthreads=cores).retrieve(6)
+        secs = time.perf_counter() - t
+        nbytes = sum(xs.nbytes for xs in sample)
+        oracle["single_core" if cores == 1 else "all_cores"] = {
+            "gbs": round(2 * nbytes / secs / 1e9, 5), "cores": cores,
+            "sample": "512^2 corner of the first 2D field and 64^3 corner of the first 3D field, "
+                      "compress + retrieval at k = 6 (bytes counted twice)"}
     return {"workload": BATCH_WORKLOAD, "fields": len(shapes), "raw_bytes": raw,
             "compress": {"batched_gbs": round(raw / (ms_b * 1e-3) / 1e9, 3), "batched_ms": round(ms_b, 3),
                          "per_field_loop_gbs": round(raw / (ms_l * 1e-3) / 1e9, 3),
@@ -503,7 +547,8 @@ def run_batched(args, device):
                           "chunks_per_item": info["chunks_per_item"], "items_per_claim": info["items_per_claim"],
                           "candidate_ms": [round(v, 3) for v in info["candidate_ms"]],
                           "first_call_s": round(t_tune, 3)},
-            "graph": bool(info["graph"]), "timing": "CUDA events around whole calls (host work included)"}
+            "graph": bool(info["graph"]), "timing": "CUDA events around whole calls (host work included)",
+            "oracle": oracle}
 
 
 def run_lossless(device):
@@ -532,9 +577,221 @@ def run_lossless(device):
     return out
 
 
-def oracle_sample(fields_np, sub, nthreads):
+class L2Flush:
+    """Writes a buffer larger than the 129 MB L2 between timed launches of a
+    small configuration, so that no launch starts with its inputs cached."""
+
+    def __init__(self, device):
+        import torch
+
+        self.buf = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=device)  # 256 MB
+
+    def __call__(self):
+        self.buf.fill_(1.0)
+
+
+def timed_events(fn, reps, flush=None):
+    """Mean ms of fn over reps launches, each bracketed by CUDA events on the
+    current stream (the flush, if any, runs outside the brackets)."""
+    import torch
+
+    total = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    return total / reps
+
+
+def run_config1(args, device, nthreads):
+    """The small plain-method configuration: a 64^3 float64 sum of 32 random
+    anisotropic Gaussians plus N(0, 1e-3) noise, 4 components, tau_i =
+    2^-4i * range (Delta = 4): compress, then retrieval at every k.  The field
+    (2 MiB) fits in L2, so L2 is flushed before every timed launch.  The
+    oracle is timed on the same field, whole, on one core and on all cores."""
+    import torch
+
+    import oracle as O
+    import paper_2308_11759_gb300 as pcz
+    import synth_fields as S
+
+    xn = S.gaussians((64, 64, 64), seed=1)
+    x = torch.from_numpy(xn).to(device)
+    tau = pcz.field_tau_schedule(x, "binary", 4, param=4)
+    flush = L2Flush(device)
+    reps = max(5, args.steps)
+    st = pcz.compress(x, tau)
+    pcz.timing_enable(True)
+    ms_c = timed_events(lambda: pcz.compress(x, tau).close(), reps, flush)
+    kt = pcz.timing_read()
+    out = torch.empty_like(x)
+    ms_r = []
+    for k in range(1, 5):
+        ms_r.append(timed_events(lambda: st.retrieve(k=k, out=out), reps, flush))
+    kt2 = pcz.timing_read()
+    pcz.timing_enable(False)
+    fb = x.numel() * 8
+    cb, rb, pay = algorithmic_bytes(st, fb)
+    hbm, _ = peaks()
+    k_comp_ms = kt["compress"][0] / max(kt["compress"][1], 1)
+    k_ret_ms = (kt2["retrieve"][0] - kt["retrieve"][0]) / max(kt2["retrieve"][1] - kt["retrieve"][1], 1)
+    st.close()
+    # the oracle on the whole field: one core (the paper's mode) and all cores
+    oc = {}
+    for cores in (1, nthreads):
+        t = time.perf_counter()
+        s = O.Streams(xn, tau, nthreads=cores)
+        for k in range(1, 5):
+            s.retrieve(k)
+        secs = time.perf_counter() - t
+        oc[cores] = {"value": round(fb * 5 / secs / 1e9, 5), "unit": "GB/s", "cores": cores, "seconds": round(secs, 3)}
+    return {"workload": "64^3 float64 sum of 32 Gaussians + N(0, 1e-3) noise, 4 components, tau_i = 2^-4i range",
+            "compress": {"ms": round(ms_c, 4), "gbs": round(fb / (ms_c * 1e-3) / 1e9, 2),
+                         "kernel_ms": round(k_comp_ms, 4),
+                         "roofline_frac_kernel": round(cb / (k_comp_ms * 1e-3) / 1e9 / hbm, 5)},
+            "retrieve": {"ms_per_k": [round(v, 4) for v in ms_r],
+                         "gbs": round(4 * fb / (sum(ms_r) * 1e-3) / 1e9, 2),
+                         "kernel_ms_mean": round(k_ret_ms, 4),
+                         "roofline_frac_kernel": round((sum(rb) / 4) / (k_ret_ms * 1e-3) / 1e9 / hbm, 5)},
+            "rates_bits_per_value": [round(8 * p / (fb / 8), 4) for p in pay],
+            "timing": "CUDA events around whole C-ABI calls (host work included), L2 flushed before each",
+            "oracle_single_core": oc[1], "oracle_all_cores": oc[nthreads]}
+
+
+def run_config5(args, device, nthreads):
+    """The near-lossless large configuration: a 1024^3 float64 k^-5/3 field plus
+    sharp tanh fronts (8 GiB), 12 components, tau_i = 10^-i * range: compress,
+    the full progressive sweep (retrieve k = 1, then refine in place up to 12),
+    and a mixed-tolerance query stream through the batched, cached server and
+    through the plain pipeline.  The oracle is timed on a 128^3 corner and
+    extrapolated per brick (bricks are coded independently)."""
+    import torch
+
+    import oracle as O
+    import paper_2308_11759_gb300 as pcz
+    import synth_fields as S
+
+    n = 12
+    size = args.c5_size
+    x = S.fronts((size, size, size), seed=5, dtype=np.float64, device=device).contiguous()
+    tau = pcz.field_tau_schedule(x, "decade", n, param=1)
+    xs128 = np.ascontiguousarray(x[:min(128, size), :min(128, size), :min(128, size)].cpu().numpy())
+    xs64 = np.ascontiguousarray(xs128[:64, :64, :64])
+    torch.cuda.synchronize()
+    fb = x.numel() * 8
+    st = pcz.compress(x, tau)
+    st.close()
+    reps = 2
+    pcz.timing_enable(True)
+    holder = {}
+
+    def comp():
+        if "st" in holder:
+            holder.pop("st").close()
+        holder["st"] = pcz.compress(x, tau)
+
+    ms_c = timed_events(comp, reps)
+    kt = pcz.timing_read()
+    st = holder["st"]
+    buf = torch.empty_like(x)
+
+    def sweep():
+        st.retrieve(k=1, out=buf)
+        for k in range(2, n + 1):
+            st.refine(k - 1, k, buf)
+
+    ms_s = timed_events(sweep, reps)
+    kt2 = pcz.timing_read()
+    pcz.timing_enable(False)
+    eq1 = []
+    for k in (1, 6, 12):
+        st.retrieve(k=k, out=buf)
+        eq1.append(float((x - buf).abs().max().item()) <= tau[k - 1])
+    hbm, _ = peaks()
+    cb, rb, pay = algorithmic_bytes(st, fb)
+    k_comp_ms = kt["compress"][0] / max(kt["compress"][1], 1)
+    # sweep bytes: every component read once, x~ read and written per refinement
+    sweep_bytes = sum(pay) + n * (st.info(0)[2]) + fb + (n - 1) * 2 * fb
+    k_sweep_ms = kt2["retrieve"][0] - kt["retrieve"][0]
+    del buf
+    # the mixed-tolerance query stream: brick-aligned boxes with sides log-uniform
+    # in [8, 512], relative tolerance log-uniform in [1e-12, 1e-1], Poisson arrivals
+    rng = np.random.default_rng(np.random.PCG64(55))
+    nq = args.c5_queries
+    arr = np.cumsum(rng.exponential(1.0 / 1000.0, nq))
+    arr -= arr[0]
+    lo_v, hi_v = pcz.field_range(x)
+    qs = []
+    for _ in range(nq):
+        lo, hi = [], []
+        for _a in range(3):
+            side = min(max(4 * int(round(np.exp(rng.uniform(np.log(8.0), np.log(512.0))) / 4.0)), 8), size)
+            o = 4 * int(rng.integers(0, (size - side) // 4 + 1))
+            lo.append(o)
+            hi.append(o + side)
+        qs.append((0, (lo, hi), 10.0 ** rng.uniform(-12.0, -1.0) * (hi_v - lo_v), 0))
+    del x
+    torch.cuda.empty_cache()
+    serve = {}
+    for name, kw in (("batched", {"max_batch": 256}), ("plain", {"serial": True, "cache": False})):
+        srv = pcz.Server(64 * 10 ** 9, **kw)
+        srv.add_field(st)
+        srv.replay(qs[:16], [0.0] * 16)
+        srv.reset_cache()
+        lat, stats = srv.replay(qs, arr.tolist())
+        srv.close()
+        lat_ms = 1e3 * lat
+        serve[name] = {"p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                       "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                       "throughput_qps": round(stats["queries"] / stats["wall_s"], 1),
+                       "gbs_out": round(stats["bytes_out"] / stats["wall_s"] / 1e9, 3),
+                       "mean_batch": round(stats["queries"] / max(stats["batches"], 1), 2)}
+    st.close()
+    torch.cuda.empty_cache()
+    # the oracle on corners of the same field, extrapolated per brick: one core
+    # on 64^3, all cores on 128^3
+    oc = {}
+    for cores, corner in ((1, xs64), (nthreads, xs128)):
+        sub = corner.shape[0]
+        t = time.perf_counter()
+        s = O.Streams(corner, tau, nthreads=cores)
+        secs_c = time.perf_counter() - t
+        t = time.perf_counter()
+        xk = s.retrieve(1)
+        for k in range(2, n + 1):
+            xk = s.retrieve(k, k0=k - 1, inout=xk)
+        secs_s = time.perf_counter() - t
+        scale = (size / sub) ** 3
+        oc[cores] = {"compress_gbs": round(corner.nbytes / secs_c / 1e9, 5),
+                     "sweep_gbs": round(n * corner.nbytes / secs_s / 1e9, 5), "cores": cores,
+                     "sample": f"{sub}^3 corner, extrapolated x{scale:.0f} by bricks",
+                     "compress_s_extrapolated": round(secs_c * scale, 1),
+                     "sweep_s_extrapolated": round(secs_s * scale, 1)}
+    return {"workload": f"{size}^3 float64 k^-5/3 field + 24 tanh fronts, 12 components, tau_i = 10^-i range",
+            "compress": {"ms": round(ms_c, 3), "gbs": round(fb / (ms_c * 1e-3) / 1e9, 2),
+                         "kernel_ms": round(k_comp_ms, 3),
+                         "roofline_frac_kernel": round(cb / (k_comp_ms * 1e-3) / 1e9 / hbm, 5)},
+            "progressive_sweep": {"ms": round(ms_s, 3), "gbs_out": round(n * fb / (ms_s * 1e-3) / 1e9, 2),
+                                  "kernel_ms": round(k_sweep_ms / reps, 3),
+                                  "roofline_frac_kernels": round(sweep_bytes / (k_sweep_ms / reps * 1e-3) / 1e9 / hbm, 5)},
+            "eq1_holds_k1_k6_k12": eq1,
+            "rates_bits_per_value": [round(8 * p / (fb / 8), 4) for p in pay],
+            "query_stream": dict(serve, queries=nq, rate_per_s=1000,
+                                 boxes="brick-aligned, sides log-uniform in [8, 512]",
+                                 tolerance="relative, log-uniform in [1e-12, 1e-1]"),
+            "oracle_single_core": oc[1], "oracle_all_cores": oc[nthreads]}
+
+
+def oracle_sample(fields_np, sub, nthreads, per_dtype=None):
     """Times the CPU oracle on a sub^3 corner of each field: Algorithm 1 then
-    Algorithm 2 at every k.  Returns (GB/s of raw bytes, seconds, description)."""
+    Algorithm 2 at every k.  Returns (GB/s of raw bytes, seconds, description);
+    per_dtype, if a dict, receives each field's compress and retrieval GB/s."""
     import oracle as O
 
     total_bytes = 0
@@ -542,10 +799,16 @@ def oracle_sample(fields_np, sub, nthreads):
     for name, x in fields_np.items():
         xs = np.ascontiguousarray(x[:sub, :sub, :sub])
         tau = O.tau_decade(O.value_range(xs), N_COMP)
+        a = time.perf_counter()
         s = O.Streams(xs, tau, nthreads=nthreads)
+        b = time.perf_counter()
         for k in range(1, N_COMP + 1):
             s.retrieve(O.query_k(tau, tau[k - 1]))
+        c = time.perf_counter()
         total_bytes += xs.nbytes * (1 + N_COMP)
+        if per_dtype is not None:
+            per_dtype[name] = {"compress_gbs": round(xs.nbytes / (b - a) / 1e9, 5),
+                               "retrieve_gbs": round(N_COMP * xs.nbytes / (c - b) / 1e9, 5)}
     secs = time.perf_counter() - t
     desc = f"{sub}^3 corner of each field (f32 and f64), compress + retrieval at every k"
     return total_bytes / secs / 1e9, secs, desc
@@ -574,6 +837,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=10000)
     ap.add_argument("--serve-size", type=int, default=256)
+    ap.add_argument("--no-configs", action="store_true", help="skip the 64^3 and 1024^3 configuration legs")
+    ap.add_argument("--c5-size", type=int, default=1024)
+    ap.add_argument("--c5-queries", type=int, default=2000)
     args = ap.parse_args()
     rank, world, local = dist_setup()
     nthreads = os.cpu_count() or 1
@@ -617,19 +883,24 @@ def main():
         torch.cuda.empty_cache()
         serving = run_serving(args, device)
     lossless = None if args.no_lossless else run_lossless(device)
+    configs = None
+    if not args.no_configs:
+        configs = {"c1_64cube_f64": run_config1(args, device, nthreads),
+                   "c5_1024cube_f64_fronts": run_config5(args, device, nthreads)}
     batched = None if args.no_batched else run_batched(args, device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fields_np = {k: v[: args.sample, : args.sample, : args.sample].cpu().numpy() for k, v in r["fields"].items()}
-        v, s, desc = oracle_sample(fields_np, args.sample, nthreads)
+        pdN, pd1 = {}, {}
+        v, s, desc = oracle_sample(fields_np, args.sample, nthreads, pdN)
         cpu = {"value": round(v, 5), "unit": "GB/s", "cores": nthreads, "kind": "oracle", "sample": desc,
-               "seconds": round(s, 2)}
+               "seconds": round(s, 2), "per_dtype": pdN}
         # the paper's own mode: one core, on a smaller corner of the same fields
         sub1 = max(4, args.sample // 2)
-        v1, s1, desc1 = oracle_sample(fields_np, sub1, 1)
+        v1, s1, desc1 = oracle_sample(fields_np, sub1, 1, pd1)
         cpu["single_core"] = {"value": round(v1, 5), "unit": "GB/s", "cores": 1, "sample": desc1,
-                              "seconds": round(s1, 2)}
+                              "seconds": round(s1, 2), "per_dtype": pd1}
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -653,12 +924,14 @@ def main():
             "clocks": r["clocks"],
             "gpu_launches": r["launches"],
             "kernels": r["kernels"],
+            "per_dtype": r["per_dtype"],
             "rates_bits_per_value": {k: v["rates"] for k, v in r["info"].items()},
             "computed_tolerances": {k: v["measured_over_tau"] for k, v in r["info"].items()},
             "accuracy_gain": r["gain"],
             "progressive_sweep": dict(r["sweep"], note="retrieve k=1 then refine k-1 -> k in place, k = 2..%d; "
                                       "outside the timed step, not part of value" % N_COMP),
             "lossless": lossless,
+            "configurations": configs,
             "batched": batched,
             "serving": serving,
         }
