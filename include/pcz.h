@@ -290,16 +290,23 @@ pc_status pc_compress_noalloc(const void *d_field, const int64_t *dims, int ndim
  * bit: x~_k of pc_retrieve on the same box.  Bricks a query produced in full
  * at a k above their cached one are written back into the cache.
  *
- * Queries are batched continuously: each batch is one launch of the
- * retrieval kernel over every query admitted for it (all of one dtype), and
- * the next batch is admitted and launched while the previous one runs.  A
- * query is admitted when its output box fits in the arena: the part of
- * hbm_budget_bytes left after the fields' streams, their caches and the
- * server's own buffers.
+ * Queries are batched continuously by a dispatcher thread of the server:
+ * queries are admitted in submission order while their output boxes fit in
+ * the arena (the part of hbm_budget_bytes left after the fields' streams,
+ * their caches and the server's own buffers), and the admitted queries of one
+ * dtype are launched as one batch -- one launch of the retrieval kernel over
+ * all their boxes -- into a free slot.  Up to 4 slots (1 in PC_SERVE_SERIAL
+ * mode) each have their own CUDA stream, so a batch admitted while others
+ * run executes concurrently with them on the device.  A batch whose brick
+ * region of a field overlaps that of an in-flight batch waits for it (the
+ * cache reads and write-backs of a brick stay ordered); other batches do not
+ * wait.  A host function queued behind every batch signals its completion:
+ * no thread polls the GPU.
  *
  * The server reads the pc_streams objects given to it, which must stay alive
- * and unchanged until pc_server_free.  All work runs on cuda_stream.  Only 3D
- * fields are served.
+ * and unchanged until pc_server_free.  The first query (submit or replay)
+ * starts the dispatcher; its batches run after the work queued on the
+ * cuda_stream given at creation.  Only 3D fields are served.
  */
 typedef struct pc_server pc_server; /* opaque */
 
@@ -321,6 +328,7 @@ typedef struct {
   uint64_t max_batch;          /* most queries in one batch */
   uint64_t peak_device_bytes;  /* fields, caches, buffers and the arena's largest use */
   uint64_t arena_bytes;        /* size of the result arena */
+  uint64_t max_inflight;       /* most batches in flight at once */
 } pc_serve_stats;
 
 /* Creates a server.  max_batch (1..65535) bounds the queries of one batch;
@@ -335,10 +343,11 @@ pc_status pc_server_create(uint64_t hbm_budget_bytes, int max_batch, int flags, 
  * budget.  Fields are added before the first replay. */
 pc_status pc_server_add_field(pc_server *srv, const pc_streams *s, int *field);
 
-/* Runs nq queries as a request stream: query j arrives arrival_s[j] seconds
- * (non-decreasing) after the call starts, and the call returns when all are
- * served.  latency_s[j] (host, nq doubles) receives the time from its arrival
- * to the host seeing its batch complete.  d_out, if not NULL, holds nq device
+/* Runs nq queries as a recorded request stream through the same dispatcher:
+ * query j is submitted arrival_s[j] seconds (non-decreasing) after the call
+ * starts (the call sleeps between arrivals), and the call returns when all
+ * are served.  latency_s[j] (host, nq doubles) receives the time from its arrival
+ * to its batch's completion on the device (signalled to the host).  d_out, if not NULL, holds nq device
  * pointers (NULL entries allowed) that receive a copy of each result box (x
  * fastest, dtype of the field).  stats may be NULL.  Every query is checked
  * before any GPU work (PC_ERR_ARG, PC_ERR_TOL_UNREACHABLE, or PC_ERR_OOM for
@@ -346,7 +355,26 @@ pc_status pc_server_add_field(pc_server *srv, const pc_streams *s, int *field);
 pc_status pc_server_replay(pc_server *srv, const pc_query *queries, const double *arrival_s, int nq,
                            void *const *d_out, double *latency_s, pc_serve_stats *stats);
 
-/* Forgets every cached partial sum (synchronises cuda_stream). */
+/* Online serving.  pc_server_submit queues one query (checked at once:
+ * PC_ERR_ARG, PC_ERR_TOL_UNREACHABLE, or PC_ERR_OOM for a box larger than the
+ * arena) and returns without waiting; *ticket identifies it.  d_out, if not
+ * NULL, is a device buffer that receives a copy of the result box (x fastest,
+ * dtype of the field) before the query counts as done.  Its arrival time is
+ * the moment of the call.  pc_server_poll reports without blocking whether
+ * the query is done (*done 1) and then its latency, from submission to the
+ * moment its batch completed on the device (*latency_s, seconds, may be
+ * NULL).  pc_server_wait blocks until the query is done or timeout_s seconds
+ * have passed (timeout_s < 0: no limit) and reports the same.  A CUDA failure
+ * of a batch is reported by the calls that ask about it.  Thread-safe: any
+ * thread may submit, poll and wait. */
+pc_status pc_server_submit(pc_server *srv, const pc_query *query, void *d_out, uint64_t *ticket);
+pc_status pc_server_poll(pc_server *srv, uint64_t ticket, int *done, double *latency_s);
+pc_status pc_server_wait(pc_server *srv, uint64_t ticket, double timeout_s, int *done, double *latency_s);
+
+/* Counters since the server was created (wall_s: since the first query). */
+pc_status pc_server_stats(pc_server *srv, pc_serve_stats *stats);
+
+/* Forgets every cached partial sum (waits until no batch is queued or running). */
 pc_status pc_server_reset_cache(pc_server *srv);
 
 /* Releases the server and its device memory (not the streams).  NULL is a no-op. */

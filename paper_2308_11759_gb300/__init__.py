@@ -45,7 +45,7 @@ class Query(C.Structure):
 class ServeStats(C.Structure):
     _fields_ = [("wall_s", C.c_double), ("batches", C.c_uint64), ("queries", C.c_uint64),
                 ("bytes_out", C.c_uint64), ("max_batch", C.c_uint64), ("peak_device_bytes", C.c_uint64),
-                ("arena_bytes", C.c_uint64)]
+                ("arena_bytes", C.c_uint64), ("max_inflight", C.c_uint64)]
 
 
 PC_SERVE_NO_CACHE, PC_SERVE_SERIAL = 1, 2
@@ -96,6 +96,10 @@ def lib():
             "pc_server_replay": [vp, C.POINTER(Query), dp, C.c_int, C.POINTER(vp), dp, C.POINTER(ServeStats)],
             "pc_server_reset_cache": [vp],
             "pc_server_free": [vp],
+            "pc_server_submit": [vp, C.POINTER(Query), vp, u64p],
+            "pc_server_poll": [vp, C.c_uint64, ip, dp],
+            "pc_server_wait": [vp, C.c_uint64, C.c_double, ip, dp],
+            "pc_server_stats": [vp, C.POINTER(ServeStats)],
             "pc_tau_schedule": [C.c_int, C.c_double, C.c_int, C.c_int, dp],
             "pc_field_tau_schedule": [vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, vp, dp],
             "pc_lossless_sweep": [vp, i64p, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.POINTER(vp), ip, dp],
@@ -443,6 +447,42 @@ class Server:
         _check(lib().pc_server_replay(self._h, qa, arr, nq, outp, lat, C.byref(st)))
         stats = {name: getattr(st, name) for name, _ in ServeStats._fields_}
         return np.frombuffer(lat, dtype=np.float64, count=nq).copy(), stats
+
+    def _query(self, field, box, tau, k):
+        known = 0 <= field < len(self._fields)  # the library rejects other indices
+        shape = self._fields[field].shape if known else tuple(box[1])
+        b, _ = _box(box, shape)
+        q = Query()
+        q.field = int(field)
+        q.k = int(k)
+        q.tau = float(tau)
+        q.box = b if b is not None else _box(([0] * len(shape), list(shape)), shape)[0]
+        return q
+
+    def submit(self, field, box, tau=0.0, k=0, out=None) -> int:
+        """Online: queues one query (k = 0: k from tau) and returns its ticket at
+        once; out (a CUDA tensor of the box's shape, or None) receives the result."""
+        t = C.c_uint64()
+        q = self._query(field, box, tau, k)
+        _check(lib().pc_server_submit(self._h, C.byref(q), _ptr(out) if out is not None else None, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """(done, latency in seconds or None) without blocking."""
+        d, lat = C.c_int(), C.c_double()
+        _check(lib().pc_server_poll(self._h, int(ticket), C.byref(d), C.byref(lat)))
+        return bool(d.value), (lat.value if d.value else None)
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        """Blocks until the query is done (or the timeout passes); (done, latency)."""
+        d, lat = C.c_int(), C.c_double()
+        _check(lib().pc_server_wait(self._h, int(ticket), float(timeout_s), C.byref(d), C.byref(lat)))
+        return bool(d.value), (lat.value if d.value else None)
+
+    def stats(self):
+        st = ServeStats()
+        _check(lib().pc_server_stats(self._h, C.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServeStats._fields_}
 
     def reset_cache(self):
         _check(lib().pc_server_reset_cache(self._h))

@@ -48,7 +48,7 @@ def test_struct_sizes(L):
 
     assert C.sizeof(P.Box) == 48
     assert C.sizeof(P.Query) == 64  # int, int, double, pc_box
-    assert C.sizeof(P.ServeStats) == 56
+    assert C.sizeof(P.ServeStats) == 64
 
 
 def test_version_and_error_text(L):

@@ -194,3 +194,52 @@ def test_errors(P, fields):
         small.replay([(0, full, 0.0, 8)], [0.0])
     assert e.value.name == "PC_ERR_OOM"
     small.close()
+
+
+def test_online_submit_poll_wait(P, fields):
+    """Online serving: queries submitted one at a time from one thread while a
+    second thread waits for them; every result equals the query run alone, and
+    with the cache off (no ordering between batches) batches overlap on the
+    device (more than one in flight)."""
+    import threading
+    import time
+
+    qs = _queries(fields, 300, seed=7)
+    want = [_alone(P, fields, q) for q in qs]
+    for cache in (False, True):
+        srv = P.Server(8 << 30, max_batch=16, cache=cache)
+        for _, _, _, st in fields:
+            srv.add_field(st)
+        outs = [torch.empty_like(w) for w in want]
+        tickets = [None] * len(qs)
+        lats = [None] * len(qs)
+        ready = threading.Semaphore(0)
+
+        def waiter():
+            for j in range(len(qs)):
+                ready.acquire()
+                done, lat = srv.wait(tickets[j], timeout_s=30.0)
+                assert done
+                lats[j] = lat
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        rng = np.random.default_rng(8)
+        for j, (f, box, t, k) in enumerate(qs):
+            tickets[j] = srv.submit(f, box, tau=t, k=k, out=outs[j])
+            ready.release()
+            if rng.random() < 0.1:
+                time.sleep(float(rng.exponential(2e-4)))
+        th.join()
+        for o, w, q in zip(outs, want, qs):
+            assert _same(o, w), q
+        assert all(lat is not None and lat > 0 for lat in lats)
+        assert srv.poll(tickets[0])[0]
+        st = srv.stats()
+        assert st["queries"] == len(qs)
+        if not cache:
+            assert st["max_inflight"] >= 2
+        with pytest.raises(P.PczError) as e:
+            srv.poll(10 ** 9)
+        assert e.value.name == "PC_ERR_ARG"
+        srv.close()
