@@ -556,7 +556,14 @@ def run_batched(args, device):
             "bits_per_value": round(bits, 3),
             "autotuner": {"schedule": info["schedule"], "order": info["order"],
                           "chunks_per_item": info["chunks_per_item"], "items_per_claim": info["items_per_claim"],
+                          "ctas_per_sm_3d": info["ctas_per_sm"], "warps_per_cta_1d2d": info["warps_small"],
+                          "one_kernel_for_both": bool(info["mixed"]),
+                          "candidates": "3D CTAs of 16 warps per SM {2, 1} x 1D/2D warps per CTA {4, 8, 16}, and "
+                                        "for 2 CTAs: 1D/2D warps {2, 4, 8, 16} x chunks per warp per item {1, 2} "
+                                        "(two kernels); one kernel for both with 1 or 2 chunks per warp; two items "
+                                        "per claim or the fields in the given order for 3 shapes",
                           "candidate_ms": [round(v, 3) for v in info["candidate_ms"]],
+                          "spread": round(max(info["candidate_ms"]) / min(info["candidate_ms"]) - 1.0, 4),
                           "first_call_s": round(t_tune, 3)},
             "graph": bool(info["graph"]), "timing": "CUDA events around whole calls (host work included)",
             "oracle": oracle}

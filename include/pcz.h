@@ -385,13 +385,18 @@ pc_status pc_server_free(pc_server *srv);
  * the fields' shapes, the type and the number of components; each
  * pc_batch_compress call then codes one set of fields of those shapes (new
  * values and tolerances) in one persistent kernel launch over all the
- * fields' chunks -- 3D chunks by whole CTAs, 1D/2D chunks by single warps --
+ * fields' chunks -- 3D chunks by whole CTAs of 16 warps in one kernel and,
+ * on a parallel branch, 1D/2D chunks by single warps in a second one, or
+ * both in one kernel --
  * followed by one segmented scan (per field and component) and one packing
- * launch.  The launches up to the scan are captured in a CUDA graph when the
- * plan is created and replayed on every call.  On the plan's first call an
- * autotuner times a fixed set of schedules (field order, chunks per work
- * item, items per claim) on that batch and keeps the fastest
- * (pc_batch_info).  The result of every call is exactly what pc_compress
+ * launch.  The launches up to the scan are captured in CUDA graphs when the
+ * plan is created (one per kernel shape) and replayed on every call.  On the
+ * plan's first call an autotuner times a fixed set of 16 schedules on that
+ * batch and keeps the fastest (pc_batch_info): CTAs of 16 warps per SM for
+ * the 3D kernel (1 at up to 128 registers per thread, or 2 at 64), warps per
+ * CTA of the 1D/2D kernel (2 to 16), chunks per warp in a 1D/2D work item
+ * (1 or 2), items per claim (1 or 2), or instead one kernel of 16-warp CTAs
+ * that takes the items of both parts from one queue.  The result of every call is exactly what pc_compress
  * gives for each field on its own, bit for bit.
  *
  *   pc_batch_create: nfields >= 1; dims: 3 extents per field (x first,
@@ -413,9 +418,11 @@ typedef struct {
   int chunks_per_item;   /* chunks of a 1D/2D field per work item */
   int items_per_claim;   /* work items a CTA claims per atomic */
   int candidates;        /* schedules timed by the autotuner */
-  int grid;              /* persistent CTAs */
+  int grid;              /* persistent CTAs of the 3D kernel */
   int graph;             /* 1 when the launches run as a CUDA graph */
-  int pad_;
+  int ctas_per_sm;       /* CTAs of 16 warps per SM of the 3D kernel variant (1 or 2) */
+  int warps_small;       /* warps per CTA of the 1D/2D kernel (2, 4, 8 or 16) */
+  int mixed;             /* 1 when one kernel codes both parts from one queue */
   uint64_t calls;        /* pc_batch_compress calls so far */
   double candidate_ms[16]; /* the autotuner's timings (ms) */
 } pc_batch_info_t;

@@ -54,7 +54,8 @@ PC_SERVE_NO_CACHE, PC_SERVE_SERIAL = 1, 2
 class BatchInfo(C.Structure):
     _fields_ = [("schedule", C.c_int), ("order", C.c_int), ("chunks_per_item", C.c_int),
                 ("items_per_claim", C.c_int), ("candidates", C.c_int), ("grid", C.c_int), ("graph", C.c_int),
-                ("pad_", C.c_int), ("calls", C.c_uint64), ("candidate_ms", C.c_double * 16)]
+                ("ctas_per_sm", C.c_int), ("warps_small", C.c_int), ("mixed", C.c_int), ("calls", C.c_uint64),
+                ("candidate_ms", C.c_double * 16)]
 
 
 _lib = None
@@ -366,7 +367,7 @@ class Batch:
     def info(self):
         inf = BatchInfo()
         _check(lib().pc_batch_info(self._h, C.byref(inf)))
-        d = {name: getattr(inf, name) for name, _ in BatchInfo._fields_ if name not in ("pad_", "candidate_ms")}
+        d = {name: getattr(inf, name) for name, _ in BatchInfo._fields_ if name != "candidate_ms"}
         d["candidate_ms"] = [inf.candidate_ms[i] for i in range(inf.candidates)]
         return d
 

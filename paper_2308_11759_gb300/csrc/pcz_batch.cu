@@ -2,18 +2,23 @@
 // fields of uneven sizes and dimensionalities in one persistent launch, and
 // Algorithm 2 (Sec. 4.2) over a batch of boxes of several fields.
 //
-// Construction: persistent CTAs of 512 threads claim items from a global
-// work counter.  An item is one chunk of 32 bricks of a 3D field (the whole
-// CTA codes it, as in pcz_compress.cu) or a run of chunks of a 1D or 2D field
-// (each warp codes one chunk, a brick per lane, as in pcz_small.cu).  All
-// fields share one scratch pool and one set of chunk arrays; a segmented scan
-// (one segment per field and component) places every chunk in its
-// component's stream, and a packing kernel copies the chunks there.  The
-// schedule (field order, chunks per item, items per claim) is picked by a
-// small autotuner that times the candidates on the plan's first batch.  The
-// launches up to the scan are captured once in a CUDA graph; the pointers and
-// tolerances of each call reach the kernels through parameter blocks that the
-// graph copies from pinned host memory, so one graph serves every call.
+// Construction: two kernels run side by side (two branches of one CUDA
+// graph), or one kernel does both parts.  In the 3D kernel, CTAs of 512
+// threads claim items from a work counter; an item is one chunk of 32 bricks of a 3D field, which the
+// whole CTA codes as pcz_compress.cu does.  In the 1D/2D kernel, CTAs of a
+// few warps claim items of several chunks of a 1D or 2D field from a second
+// counter, and each warp codes one chunk at a time, a brick per lane, as
+// pcz_small.cu does (no register cap: a 2D brick of float64 values lives in
+// one thread's registers).  All fields share one scratch pool and one set of
+// chunk arrays; a segmented scan (one segment per field and component) places
+// every chunk in its component's stream, and a packing kernel copies the
+// chunks there.  The schedule (field order, CTAs per SM of the 3D kernel,
+// warps per CTA and chunks per item of the 1D/2D kernel, items per claim) is
+// picked by a small autotuner that times the candidates on the plan's first
+// batch.  The launches up to the scan are captured in CUDA graphs, one per
+// kernel shape; the pointers and tolerances of each call reach the kernels
+// through parameter blocks that the graph copies from pinned host memory, so
+// one graph serves every call.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -26,24 +31,46 @@
 
 namespace pcz {
 
-template <typename T>
-__host__ __device__ constexpr size_t batch_smem() {
-  const size_t a = compress_smem3<T>();
-  const size_t b = (size_t)(kCompressThreads3 / 32) * chunk_words_small<T, 2>() * 4;
-  return a > b ? a : b;
+template <typename T, int W>
+__host__ __device__ constexpr size_t batch_small_smem() {  // a chunk buffer per warp, sized for 2D bricks
+  return (size_t)W * chunk_words_small<T, 2>() * 4;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kCompressThreads3, 1) k_compress_batch(const BatchParams* __restrict__ bp) {
+// The item of work list `bp` that `it` falls in: its slot's field, first chunk,
+// chunk count and dimensionality, written to the CTA's shared copies.
+__device__ __forceinline__ void find_item(const BatchParams* __restrict__ bp, int64_t it, int* f_out, int64_t* c0_out,
+                                          int* nch_out, int* nd_out) {
+  int lo = 0, hi = bp->nslots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bp->slot_first[mid] <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int f = bp->slot_field[lo];
+  const int w = bp->slot_width[lo];
+  const int64_t c0 = (it - bp->slot_first[lo]) * w;
+  const int64_t nch = bp->fields[f].nchunks;
+  *f_out = f;
+  *c0_out = c0;
+  *nch_out = (int)(nch - c0 < w ? nch - c0 : w);
+  *nd_out = bp->slot_ndims[lo];
+}
+
+// 3D part of a batch: CTAs of 16 warps claim chunks of the 3D
+// fields (one chunk of 32 bricks per item) and code each as pc_compress does.
+// MINB = CTAs per SM the variant is compiled for: 1 (up to 128 registers per
+// thread) or 2 (at most 64, two CTAs sharing an SM).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kCompressThreads3, MINB) k_batch3(const BatchParams* __restrict__ bp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CompressParams sP;
-  __shared__ long long s_first;
+  __shared__ long long s_first, s_chunk0;
   __shared__ int s_field, s_nchunks, s_ndims;
-  __shared__ long long s_chunk0;
   static_assert(sizeof(CompressParams) % 8 == 0, "parameter copy");
   constexpr int PW = (int)(sizeof(CompressParams) / 8);
-  constexpr int WARPS = kCompressThreads3 / 32;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t nitems = bp->nitems;
   const int per = bp->per_fetch;
   for (;;) {
@@ -55,23 +82,14 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress_batch(const B
     const int64_t last = first + per < nitems ? first + per : nitems;
     for (int64_t it = first; it < last; ++it) {
       __syncthreads();  // the previous item is done with sP and the buffers
-      if (tid == 0) {   // the item's slot, field and chunk range
-        int lo = 0, hi = bp->nslots - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (bp->slot_first[mid] <= it)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        const int f = bp->slot_field[lo];
-        const int w = bp->slot_width[lo];
-        const int64_t c0 = (it - bp->slot_first[lo]) * w;
-        const int64_t nch = bp->fields[f].nchunks;
+      if (tid == 0) {
+        int f, nch, nd;
+        int64_t c0;
+        find_item(bp, it, &f, &c0, &nch, &nd);
         s_field = f;
         s_chunk0 = c0;
-        s_nchunks = (int)(nch - c0 < w ? nch - c0 : w);
-        s_ndims = bp->slot_ndims[lo];
+        s_nchunks = nch;
+        s_ndims = nd;
       }
       __syncthreads();
       {
@@ -80,12 +98,110 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress_batch(const B
         for (int w = tid; w < PW; w += kCompressThreads3) dst[w] = src[w];
       }
       __syncthreads();
-      const int nd = s_ndims;
+      compress3_chunk<T>(sP, s_chunk0, smem);
+    }
+  }
+}
+
+// 1D/2D part of a batch: CTAs of W warps claim items of `width`
+// chunks of the 1D and 2D fields; the CTA's warps take the item's chunks one
+// at a time (a brick per lane, as in pcz_small.cu).  Float32 variants are
+// held to 128 registers so that 16 warps share an SM; float64 ones have no
+// cap, because a 2D brick of float64 values lives in one thread's registers.
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 16 / W : 1) k_batch_small(const BatchParams* __restrict__ bp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CompressParams sP;
+  __shared__ long long s_first, s_chunk0;
+  __shared__ int s_field, s_nchunks, s_ndims;
+  constexpr int PW = (int)(sizeof(CompressParams) / 8);
+  constexpr int NT = 32 * W;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t nitems = bp->nitems;
+  const int per = bp->per_fetch;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_first = (long long)atomicAdd(bp->next, (unsigned long long)per);
+    __syncthreads();
+    const int64_t first = s_first;
+    if (first >= nitems) break;
+    const int64_t last = first + per < nitems ? first + per : nitems;
+    for (int64_t it = first; it < last; ++it) {
+      __syncthreads();
+      if (tid == 0) {
+        int f, nch, nd;
+        int64_t c0;
+        find_item(bp, it, &f, &c0, &nch, &nd);
+        s_field = f;
+        s_chunk0 = c0;
+        s_nchunks = nch;
+        s_ndims = nd;
+      }
+      __syncthreads();
+      {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(bp->fields + s_field);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&sP);
+        for (int w = tid; w < PW; w += NT) dst[w] = src[w];
+      }
+      __syncthreads();
       const int64_t c0 = s_chunk0;
       const int nch = s_nchunks;
-      if (nd == 3) {
+      if (s_ndims == 2) {
+        uint32_t* cbuf = reinterpret_cast<uint32_t*>(smem) + (size_t)warp * chunk_words_small<T, 2>();
+        for (int c = warp; c < nch; c += W) compress_small_chunk<T, 2>(sP, c0 + c, cbuf);
+      } else {
+        uint32_t* cbuf = reinterpret_cast<uint32_t*>(smem) + (size_t)warp * chunk_words_small<T, 1>();
+        for (int c = warp; c < nch; c += W) compress_small_chunk<T, 1>(sP, c0 + c, cbuf);
+      }
+    }
+  }
+}
+
+// Both parts in one kernel: CTAs of 16 warps (up to 128 registers per thread)
+// claim items of one work list holding the 3D and the 1D/2D fields; a 3D item
+// takes the whole CTA, a 1D/2D item one chunk per warp at a time.  With one
+// queue the two kinds of work share the SMs to the end.
+template <typename T>
+__global__ void __launch_bounds__(kCompressThreads3, 1) k_batch_mixed(const BatchParams* __restrict__ bp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CompressParams sP;
+  __shared__ long long s_first, s_chunk0;
+  __shared__ int s_field, s_nchunks, s_ndims;
+  constexpr int PW = (int)(sizeof(CompressParams) / 8);
+  constexpr int WARPS = kCompressThreads3 / 32;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t nitems = bp->nitems;
+  const int per = bp->per_fetch;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_first = (long long)atomicAdd(bp->next, (unsigned long long)per);
+    __syncthreads();
+    const int64_t first = s_first;
+    if (first >= nitems) break;
+    const int64_t last = first + per < nitems ? first + per : nitems;
+    for (int64_t it = first; it < last; ++it) {
+      __syncthreads();
+      if (tid == 0) {
+        int f, nch, nd;
+        int64_t c0;
+        find_item(bp, it, &f, &c0, &nch, &nd);
+        s_field = f;
+        s_chunk0 = c0;
+        s_nchunks = nch;
+        s_ndims = nd;
+      }
+      __syncthreads();
+      {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(bp->fields + s_field);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&sP);
+        for (int w = tid; w < PW; w += kCompressThreads3) dst[w] = src[w];
+      }
+      __syncthreads();
+      const int64_t c0 = s_chunk0;
+      const int nch = s_nchunks;
+      if (s_ndims == 3) {
         compress3_chunk<T>(sP, c0, smem);
-      } else if (nd == 2) {
+      } else if (s_ndims == 2) {
         uint32_t* cbuf = reinterpret_cast<uint32_t*>(smem) + (size_t)warp * chunk_words_small<T, 2>();
         for (int c = warp; c < nch; c += WARPS) compress_small_chunk<T, 2>(sP, c0 + c, cbuf);
       } else {
@@ -97,15 +213,67 @@ __global__ void __launch_bounds__(kCompressThreads3, 1) k_compress_batch(const B
 }
 
 template <typename T>
-static int batch_grid_t() {
+__host__ __device__ constexpr size_t batch_mixed_smem() {
+  const size_t a = compress_smem3<T>();
+  const size_t b = (size_t)(kCompressThreads3 / 32) * chunk_words_small<T, 2>() * 4;
+  return a > b ? a : b;
+}
+
+template <typename T>
+static int batch_mixed_grid_t() {
   static int grid = 0;
   if (!grid) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_compress_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<T>());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_compress_batch<T>, kCompressThreads3,
-                                                      batch_smem<T>()) != cudaSuccess ||
+    cudaFuncSetAttribute(k_batch_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_mixed_smem<T>());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_mixed<T>, kCompressThreads3,
+                                                      batch_mixed_smem<T>()) != cudaSuccess ||
+        per < 1)
+      per = 1;
+    grid = (sms > 0 ? sms : 1) * per;
+  }
+  return grid;
+}
+
+int compress_batch_mixed_grid(int dtype) { return dtype == 1 ? batch_mixed_grid_t<float>() : batch_mixed_grid_t<double>(); }
+
+cudaError_t launch_compress_batch_mixed(int dtype, const BatchParams* d_bp, int grid, cudaStream_t s) {
+  if (dtype == 1)
+    k_batch_mixed<float><<<grid, kCompressThreads3, batch_mixed_smem<float>(), s>>>(d_bp);
+  else
+    k_batch_mixed<double><<<grid, kCompressThreads3, batch_mixed_smem<double>(), s>>>(d_bp);
+  return cudaGetLastError();
+}
+
+template <typename T, int MINB>
+static int batch3_grid_t() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_batch3<T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)compress_smem3<T>());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3<T, MINB>, kCompressThreads3,
+                                                      compress_smem3<T>()) != cudaSuccess ||
+        per < 1)
+      per = 1;
+    grid = (sms > 0 ? sms : 1) * per;
+  }
+  return grid;
+}
+
+template <typename T, int W>
+static int batch_small_grid_t() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_batch_small<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batch_small_smem<T, W>());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_small<T, W>, 32 * W, batch_small_smem<T, W>()) !=
+            cudaSuccess ||
         per < 1)
       per = 1;
     grid = (sms > 0 ? sms : 1) * per;
@@ -115,14 +283,55 @@ static int batch_grid_t() {
 
 uint32_t check_word_batch(int reset) { return read_check_word(reset); }
 
-int compress_batch_grid(int dtype) { return dtype == 1 ? batch_grid_t<float>() : batch_grid_t<double>(); }
+int compress_batch_grid(int dtype, int minb) {
+  if (dtype == 1) return minb == 2 ? batch3_grid_t<float, 2>() : batch3_grid_t<float, 1>();
+  return minb == 2 ? batch3_grid_t<double, 2>() : batch3_grid_t<double, 1>();
+}
 
-cudaError_t launch_compress_batch(int dtype, const BatchParams* d_bp, int grid, cudaStream_t s) {
+int compress_batch_small_grid(int dtype, int warps) {
+  if (dtype == 1)
+    return warps == 2   ? batch_small_grid_t<float, 2>()
+           : warps == 4 ? batch_small_grid_t<float, 4>()
+           : warps == 8 ? batch_small_grid_t<float, 8>()
+                        : batch_small_grid_t<float, 16>();
+  return warps == 2   ? batch_small_grid_t<double, 2>()
+         : warps == 4 ? batch_small_grid_t<double, 4>()
+         : warps == 8 ? batch_small_grid_t<double, 8>()
+                      : batch_small_grid_t<double, 16>();
+}
+
+cudaError_t launch_compress_batch(int dtype, int minb, const BatchParams* d_bp, int grid, cudaStream_t s) {
   if (dtype == 1) {
-    k_compress_batch<float><<<grid, kCompressThreads3, batch_smem<float>(), s>>>(d_bp);
+    if (minb == 2)
+      k_batch3<float, 2><<<grid, kCompressThreads3, compress_smem3<float>(), s>>>(d_bp);
+    else
+      k_batch3<float, 1><<<grid, kCompressThreads3, compress_smem3<float>(), s>>>(d_bp);
   } else {
-    k_compress_batch<double><<<grid, kCompressThreads3, batch_smem<double>(), s>>>(d_bp);
+    if (minb == 2)
+      k_batch3<double, 2><<<grid, kCompressThreads3, compress_smem3<double>(), s>>>(d_bp);
+    else
+      k_batch3<double, 1><<<grid, kCompressThreads3, compress_smem3<double>(), s>>>(d_bp);
   }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static void launch_small_t(int warps, const BatchParams* d_bp, int grid, cudaStream_t s) {
+  if (warps == 2)
+    k_batch_small<T, 2><<<grid, 64, batch_small_smem<T, 2>(), s>>>(d_bp);
+  else if (warps == 4)
+    k_batch_small<T, 4><<<grid, 128, batch_small_smem<T, 4>(), s>>>(d_bp);
+  else if (warps == 8)
+    k_batch_small<T, 8><<<grid, 256, batch_small_smem<T, 8>(), s>>>(d_bp);
+  else
+    k_batch_small<T, 16><<<grid, 512, batch_small_smem<T, 16>(), s>>>(d_bp);
+}
+
+cudaError_t launch_compress_batch_small(int dtype, int warps, const BatchParams* d_bp, int grid, cudaStream_t s) {
+  if (dtype == 1)
+    launch_small_t<float>(warps, d_bp, grid, s);
+  else
+    launch_small_t<double>(warps, d_bp, grid, s);
   return cudaGetLastError();
 }
 
@@ -150,15 +359,37 @@ struct BatchArena {
   }
 };
 
+// A schedule of the batched construction: the order of the fields' work,
+// the block shapes of the two persistent kernels and how much a claim takes.
+// A 3D item is one chunk of 32 bricks for a whole CTA of 16 warps (two bricks
+// per warp); `ctas3` such CTAs share an SM (1 at up to 128 registers per
+// thread, 2 at 64).  A 1D/2D item is warps_small * chunks_per_warp chunks
+// for a CTA of warps_small warps, one chunk (a brick per lane) per warp at a
+// time.
 struct Schedule {
-  int order;      // 0: fields in the caller's order; 1: largest first
-  int width;      // chunks per item of a 1D/2D field
-  int per_fetch;  // items per claim
+  int order;            // 0: fields in the caller's order; 1: largest first
+  int ctas3;            // CTAs per SM of the 3D kernel: 1 or 2; 0: one kernel for both parts, whose
+                        // CTAs of 16 warps take 3D and 1D/2D items from one queue
+  int warps_small;      // warps per CTA of the 1D/2D kernel: 2, 4, 8 or 16
+  int chunks_per_warp;  // chunks per warp in a 1D/2D item: 1 or 2
+  int per_fetch;        // items per claim
 };
 
-const Schedule kSchedules[] = {{1, 16, 1}, {1, 32, 1}, {1, 16, 2}, {1, 32, 2},
-                               {0, 16, 1}, {0, 32, 1}, {0, 16, 2}, {0, 32, 2}};
+const Schedule kSchedules[] = {
+    {1, 2, 4, 1, 1},  {1, 2, 8, 1, 1},  {1, 2, 16, 1, 1}, {1, 1, 4, 1, 1},  {1, 1, 8, 1, 1},  {1, 1, 16, 1, 1},
+    {1, 2, 4, 2, 1},  {1, 2, 8, 2, 1},  {1, 2, 16, 2, 1}, {1, 2, 2, 1, 1},  {1, 2, 2, 2, 1},  {1, 0, 16, 1, 1},
+    {1, 0, 16, 2, 1}, {1, 2, 8, 1, 2},  {1, 2, 16, 1, 2}, {0, 2, 16, 1, 1}};
 constexpr int kNumSchedules = (int)(sizeof(kSchedules) / sizeof(kSchedules[0]));
+constexpr int kSmallShapes[4] = {2, 4, 8, 16};
+constexpr int kVariants = 9;  // graphs: 2 x 4 two-kernel shapes and the mixed kernel
+
+// Graph of the kernel variants (3D CTAs per SM x 1D/2D warps per CTA: 0..7;
+// the single mixed kernel: 8).
+int variant_of(const Schedule& sc) {
+  if (sc.ctas3 == 0) return 8;
+  const int w = sc.warps_small == 2 ? 0 : sc.warps_small == 4 ? 1 : sc.warps_small == 8 ? 2 : 3;
+  return (sc.ctas3 - 1) * 4 + w;
+}
 
 }  // namespace
 
@@ -176,7 +407,7 @@ struct pc_batch {
   // plan-owned device scratch
   void* scratch = nullptr;
   CompressParams* d_fields = nullptr;
-  BatchParams* d_bp = nullptr;
+  BatchParams* d_bp = nullptr;  // [2]: the 3D work list, the 1D/2D work list
   ScanParams* d_sp = nullptr;
   int32_t* d_slot_field = nullptr;
   int32_t* d_slot_width = nullptr;
@@ -200,7 +431,7 @@ struct pc_batch {
   // pinned host mirrors
   void* pinned = nullptr;
   CompressParams* h_fields = nullptr;
-  BatchParams* h_bp = nullptr;
+  BatchParams* h_bp = nullptr;  // [2]
   ScanParams* h_sp = nullptr;
   int32_t* h_slot_field = nullptr;
   int32_t* h_slot_width = nullptr;
@@ -211,8 +442,14 @@ struct pc_batch {
   unsigned long long* h_segmaxerr = nullptr;
   unsigned int* h_flags = nullptr;
   unsigned long long* h_used = nullptr;
-  // graph and schedule
-  cudaGraphExec_t exec = nullptr;
+  // graphs (one per kernel variant: 3D CTAs per SM x 1D/2D warps per CTA) and schedule
+  cudaStream_t st2 = nullptr;  // the 1D/2D kernel's branch of the graph
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaGraphExec_t execs[kVariants] = {};
+  int grid_mixed = 0;
+  cudaGraphExec_t exec = nullptr;  // the current schedule's
+  int grid3[2] = {0, 0};
+  int grid_small[4] = {0, 0, 0, 0};
   int grid = 0;
   int schedule = -1;
   double tune_ms[kNumSchedules] = {};
@@ -224,8 +461,12 @@ namespace {
 void batch_release(pc_batch* B) {
   if (!B) return;
   if (B->st) cudaStreamSynchronize(B->st);
-  if (B->exec) cudaGraphExecDestroy(B->exec);
+  for (cudaGraphExec_t x : B->execs)
+    if (x) cudaGraphExecDestroy(x);
   if (B->ready) cudaEventDestroy(B->ready);
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->join) cudaEventDestroy(B->join);
+  if (B->st2) cudaStreamDestroy(B->st2);
   if (B->st) cudaStreamDestroy(B->st);
   cudaFree(B->scratch);
   cudaFree(B->pool);
@@ -233,8 +474,9 @@ void batch_release(pc_batch* B) {
   delete B;
 }
 
-// The work list of a schedule, as slots in the pinned mirrors.
-int64_t set_schedule(pc_batch* B, const Schedule& sc) {
+// The two work lists of a schedule (3D fields, then 1D/2D fields), as slots
+// in the pinned mirrors: list 0 at slot arrays [0, F), list 1 at [F, 2F).
+void set_schedule(pc_batch* B, const Schedule& sc) {
   std::vector<int> ord(B->nfields);
   std::iota(ord.begin(), ord.end(), 0);
   if (sc.order == 1) {
@@ -242,45 +484,67 @@ int64_t set_schedule(pc_batch* B, const Schedule& sc) {
       return B->nbricks[a] * (B->ndims[a] == 3 ? 4 : 1) > B->nbricks[b] * (B->ndims[b] == 3 ? 4 : 1);
     });
   }
-  int64_t items = 0;
-  for (int s = 0; s < B->nfields; ++s) {
-    const int f = ord[s];
-    const int w = B->ndims[f] == 3 ? 1 : sc.width;
-    B->h_slot_field[s] = f;
-    B->h_slot_width[s] = w;
-    B->h_slot_ndims[s] = B->ndims[f];
-    B->h_slot_first[s] = items;
-    items += (B->nchunks[f] + w - 1) / w;
+  const int F = B->nfields;
+  for (int list = 0; list < 2; ++list) {
+    int64_t items = 0;
+    int ns = 0;
+    const int base = list * F;
+    for (int f : ord) {
+      if (sc.ctas3 == 0 ? list == 1 : (B->ndims[f] == 3) != (list == 0)) continue;
+      const int w = B->ndims[f] == 3 ? 1 : sc.warps_small * sc.chunks_per_warp;
+      B->h_slot_field[base + ns] = f;
+      B->h_slot_width[base + ns] = w;
+      B->h_slot_ndims[base + ns] = B->ndims[f];
+      B->h_slot_first[base + list + ns] = items;
+      items += (B->nchunks[f] + w - 1) / w;
+      ++ns;
+    }
+    B->h_slot_first[base + list + ns] = items;
+    BatchParams& bp = B->h_bp[list];
+    bp.nslots = ns;
+    bp.nitems = items;
+    bp.per_fetch = sc.per_fetch;
   }
-  B->h_slot_first[B->nfields] = items;
-  B->h_bp->nitems = items;
-  B->h_bp->per_fetch = sc.per_fetch;
-  return items;
+  B->exec = B->execs[variant_of(sc)];
+  B->grid = sc.ctas3 == 0 ? B->grid_mixed : B->grid3[sc.ctas3 - 1];
 }
 
 // Captures H2D of the parameter blocks, the counters' reset, the batched
-// construction, the segmented scan and the D2H of the results.
-pc_status capture_graph(pc_batch* B) {
+// construction (kernel variant v: the 3D kernel for v / 3 + 1 CTAs per SM and,
+// on a parallel branch, the 1D/2D kernel with kSmallShapes[v % 3] warps per
+// CTA), the segmented scan and the D2H of the results.
+pc_status capture_graph(pc_batch* B, int v) {
   cudaStream_t st = B->st;
   cudaGraph_t g = nullptr;
   BK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaMemcpyAsync(B->d_fields, B->h_fields, sizeof(CompressParams) * B->nfields,
                                   cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_bp, B->h_bp, sizeof(BatchParams), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_bp, B->h_bp, 2 * sizeof(BatchParams), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_sp, B->h_sp, sizeof(ScanParams), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(B->d_slot_field, B->h_slot_field, 4 * (size_t)B->nfields, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(B->d_slot_field, B->h_slot_field, 8 * (size_t)B->nfields, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(B->d_slot_width, B->h_slot_width, 4 * (size_t)B->nfields, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(B->d_slot_width, B->h_slot_width, 8 * (size_t)B->nfields, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(B->d_slot_ndims, B->h_slot_ndims, 4 * (size_t)B->nfields, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(B->d_slot_ndims, B->h_slot_ndims, 8 * (size_t)B->nfields, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(B->d_slot_first, B->h_slot_first, 8 * (size_t)(B->nfields + 1), cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(B->d_slot_first, B->h_slot_first, 16 * (size_t)(B->nfields + 1), cudaMemcpyHostToDevice,
                         st);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->d_flags, 0, 16, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->d_used, 0, 16, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->d_next, 0, 16, st);
-  if (e == cudaSuccess) e = launch_compress_batch(B->dtype, B->d_bp, B->grid, st);
+  // fork: the 1D/2D kernel on the second stream, the 3D kernel on the first
+  if (v == kVariants - 1) {
+    if (e == cudaSuccess) e = launch_compress_batch_mixed(B->dtype, B->d_bp, B->grid_mixed, st);
+  } else {
+    if (e == cudaSuccess) e = cudaEventRecord(B->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->st2, B->fork, 0);
+    if (e == cudaSuccess)
+      e = launch_compress_batch_small(B->dtype, kSmallShapes[v % 4], B->d_bp + 1, B->grid_small[v % 4], B->st2);
+    if (e == cudaSuccess) e = cudaEventRecord(B->join, B->st2);
+    if (e == cudaSuccess) e = launch_compress_batch(B->dtype, v / 4 + 1, B->d_bp, B->grid3[v / 4], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B->join, 0);
+  }
   if (e == cudaSuccess) e = launch_scan_segments(B->d_sp, B->nseg, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(B->h_totals, B->d_totals, 8 * (size_t)B->nseg, cudaMemcpyDeviceToHost, st);
@@ -292,7 +556,7 @@ pc_status capture_graph(pc_batch* B) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(B->h_used, B->d_used, 8, cudaMemcpyDeviceToHost, st);
   const cudaError_t e2 = cudaStreamEndCapture(st, &g);
   if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&B->execs[v], g, 0);
   if (g) cudaGraphDestroy(g);
   if (e != cudaSuccess) return api_cuda_fail(e, "graph capture");
   return PC_OK;
@@ -359,11 +623,14 @@ pc_status pc_batch_create(int nfields, const int64_t* dims, const int* ndims, pc
   }
   cudaError_t e = cudaGetDevice(&B->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->st2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ready, cudaEventDisableTiming);
   // one scratch allocation, carved in 256-byte aligned pieces
   const size_t F = nfields, S = B->nseg, E = B->nentries;
-  const size_t sizes[] = {sizeof(CompressParams) * F, sizeof(BatchParams), sizeof(ScanParams), 4 * F, 4 * F,
-                          4 * F, 8 * (F + 1), 4 * E, 8 * E, 20 * E, 8 * E, 8 * S, 40 * S, 8 * S, 8 * S, 8 * S, 8 * S,
+  const size_t sizes[] = {sizeof(CompressParams) * F, 2 * sizeof(BatchParams), sizeof(ScanParams), 8 * F, 8 * F,
+                          8 * F, 16 * (F + 1), 4 * E, 8 * E, 20 * E, 8 * E, 8 * S, 40 * S, 8 * S, 8 * S, 8 * S, 8 * S,
                           16, 16, 16};
   size_t total = 0;
   for (size_t v : sizes) total += align256(v);
@@ -383,8 +650,8 @@ pc_status pc_batch_create(int nfields, const int64_t* dims, const int* ndims, pc
       p += align256(sizes[i]);
     }
   }
-  const size_t hsizes[] = {sizeof(CompressParams) * F, sizeof(BatchParams), sizeof(ScanParams), 4 * F, 4 * F,
-                           4 * F, 8 * (F + 1), 8 * S, 40 * S, 8 * S, 16, 16};
+  const size_t hsizes[] = {sizeof(CompressParams) * F, 2 * sizeof(BatchParams), sizeof(ScanParams), 8 * F, 8 * F,
+                           8 * F, 16 * (F + 1), 8 * S, 40 * S, 8 * S, 16, 16};
   size_t htotal = 0;
   for (size_t v : hsizes) htotal += align256(v);
   if (e == cudaSuccess) e = cudaMallocHost(&B->pinned, htotal);
@@ -423,16 +690,40 @@ pc_status pc_batch_create(int nfields, const int64_t* dims, const int* ndims, pc
     batch_release(B);
     return api_cuda_fail(e, "batch allocation");
   }
-  B->grid = compress_batch_grid(dtype);
-  // parameter blocks: fixed parts
-  BatchParams& bp = *B->h_bp;
-  bp.fields = B->d_fields;
-  bp.slot_field = B->d_slot_field;
-  bp.slot_width = B->d_slot_width;
-  bp.slot_ndims = B->d_slot_ndims;
-  bp.slot_first = B->d_slot_first;
-  bp.nslots = nfields;
-  bp.next = B->d_next;
+  // Both kernels launch a CTA per work item at most (the CTAs still claim
+  // items from their counters, so every schedule's item count is covered): the
+  // hardware then spreads the CTAs of both kernels over the SMs as they free
+  // up, and neither kernel's tail leaves SMs idle while the other has work.
+  {
+    int64_t items3 = 0, items_small[4] = {0, 0, 0, 0};  // 1D/2D items: at least one chunk per warp
+    for (int f = 0; f < nfields; ++f) {
+      if (ndims[f] == 3)
+        items3 += B->nchunks[f];
+      else
+        for (int w = 0; w < 4; ++w) items_small[w] += (B->nchunks[f] + kSmallShapes[w] - 1) / kSmallShapes[w];
+    }
+    const int64_t cap = 1 << 22;
+    for (int m = 0; m < 2; ++m) {
+      compress_batch_grid(dtype, m + 1);  // sets the kernel's shared-memory limit
+      B->grid3[m] = (int)std::max<int64_t>(std::min(items3, cap), 1);
+    }
+    for (int w = 0; w < 4; ++w) {
+      compress_batch_small_grid(dtype, kSmallShapes[w]);
+      B->grid_small[w] = (int)std::max<int64_t>(std::min(items_small[w], cap), 1);
+    }
+    B->grid_mixed = compress_batch_mixed_grid(dtype);  // persistent
+  }
+  // parameter blocks: fixed parts (list 0: 3D fields, list 1: 1D/2D fields)
+  for (int list = 0; list < 2; ++list) {
+    BatchParams& bp = B->h_bp[list];
+    bp.fields = B->d_fields;
+    bp.slot_field = B->d_slot_field + list * nfields;
+    bp.slot_width = B->d_slot_width + list * nfields;
+    bp.slot_ndims = B->d_slot_ndims + list * nfields;
+    bp.slot_first = B->d_slot_first + list * (nfields + 1);
+    bp.nslots = 0;
+    bp.next = B->d_next + list;
+  }
   ScanParams& sp = *B->h_sp;
   sp.nwords = B->d_nwords;
   sp.totals = B->d_totals;
@@ -443,12 +734,13 @@ pc_status pc_batch_create(int nfields, const int64_t* dims, const int* ndims, pc
   sp.seg_start = B->d_seg_start;
   sp.seg_len = B->d_seg_len;
   sp.nseg = B->nseg;
-  set_schedule(B, kSchedules[0]);
-  pc_status r = capture_graph(B);
+  pc_status r = PC_OK;
+  for (int v = 0; v < kVariants && r == PC_OK; ++v) r = capture_graph(B, v);
   if (r != PC_OK) {
     batch_release(B);
     return r;
   }
+  set_schedule(B, kSchedules[0]);
   *out = B;
   return PC_OK;
 }
@@ -611,9 +903,13 @@ pc_status pc_batch_info(const pc_batch* B, pc_batch_info_t* info) {
   std::memset(info, 0, sizeof(*info));
   info->schedule = B->schedule;
   if (B->schedule >= 0) {
-    info->order = kSchedules[B->schedule].order;
-    info->chunks_per_item = kSchedules[B->schedule].width;
-    info->items_per_claim = kSchedules[B->schedule].per_fetch;
+    const Schedule& sc = kSchedules[B->schedule];
+    info->order = sc.order;
+    info->chunks_per_item = sc.warps_small * sc.chunks_per_warp;
+    info->items_per_claim = sc.per_fetch;
+    info->ctas_per_sm = sc.ctas3 ? sc.ctas3 : 1;
+    info->warps_small = sc.warps_small;
+    info->mixed = sc.ctas3 == 0;
   }
   info->candidates = kNumSchedules;
   for (int c = 0; c < kNumSchedules && c < 16; ++c) info->candidate_ms[c] = B->tune_ms[c];

@@ -137,8 +137,16 @@ cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint6
 cudaError_t launch_pack(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
                         const uint64_t* word_off, const uint64_t* comp_base, uint64_t* payload, int n,
                         int64_t nchunks, cudaStream_t s);
-cudaError_t launch_compress_batch(int dtype, const BatchParams* d_bp, int grid, cudaStream_t s);
-int compress_batch_grid(int dtype);  // persistent CTAs of the batched construction kernel
+// Batched construction: the 3D part (minb: CTAs of 16 warps per SM the
+// kernel variant is built for, 1 or 2) and the 1D/2D part (warps per CTA: 2,
+// 4, 8 or 16); the grids are the persistent CTAs that fit.
+cudaError_t launch_compress_batch(int dtype, int minb, const BatchParams* d_bp, int grid, cudaStream_t s);
+int compress_batch_grid(int dtype, int minb);
+cudaError_t launch_compress_batch_small(int dtype, int warps, const BatchParams* d_bp, int grid, cudaStream_t s);
+int compress_batch_small_grid(int dtype, int warps);
+// Both parts in one kernel of 16-warp CTAs over one queue (persistent grid).
+cudaError_t launch_compress_batch_mixed(int dtype, const BatchParams* d_bp, int grid, cudaStream_t s);
+int compress_batch_mixed_grid(int dtype);
 cudaError_t launch_scan_segments(const ScanParams* d_sp, int nseg, cudaStream_t s);
 cudaError_t launch_pack_segments(const uint64_t* pool, const uint32_t* nwords, const uint64_t* chunk_pool,
                                  const uint64_t* word_off, const int64_t* seg_start, const uint64_t* seg_base,
