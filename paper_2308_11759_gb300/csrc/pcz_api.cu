@@ -512,7 +512,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
       if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, 16, st);
       if (e == cudaSuccess) {
         TimedLaunch tl(PC_KERNEL_COMPRESS, st);
-        e = launch_compress(dtype, ndims, P, st);
+        e = launch_compress(dtype, ndims, P, st, !mapped_host);
       }
       if (e == cudaSuccess) {
         TimedLaunch tl(PC_KERNEL_SCAN, st);
@@ -532,6 +532,8 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
       rc = cuda_fail(e, "compress");
     } else if (h_flags & kFlagNonFinite) {
       rc = fail(PC_ERR_NONFINITE, "the field holds a NaN or an infinity");
+    } else if (h_flags & kFlagStageTimeout) {
+      rc = fail(PC_ERR_CUDA, "a tile copy of the field into shared memory did not complete");
     } else if (h_flags & kFlagPoolOverflow) {
       rc = fail(PC_ERR_OOM, "scratch pool could not be sized");
     } else {

@@ -8,6 +8,8 @@
 #include <climits>
 #include <type_traits>
 
+#include <cuda.h>  // CUtensorMap (the type only; the library links no driver API)
+
 #include "pcz_device.cuh"
 #include "pcz_kernels.h"
 
@@ -29,13 +31,30 @@ __host__ __device__ constexpr int chunk_buf_words3() {  // u32 words, rounded to
 
 constexpr int kCompressThreads3 = 512;
 
+// The per-plane tables of a warp's two bricks share the warp's brick buffer,
+// which is free from the end of the decode-back until the next component's
+// forward transform: the plane words (8 bytes per plane) for 64-bit
+// coefficients, the plane offsets and counts (4 bytes) for 32-bit ones --
+// whichever has the buffer's element size.
 template <typename T>
-constexpr size_t compress_smem3() {
+__host__ __device__ constexpr bool planes_in_brick_buffer() {
+  return sizeof(typename Fmt<T>::S) == 8;
+}
+
+// Bytes of the staging area in front of the rest (TMA-staged form only).
+template <typename T>
+__host__ __device__ constexpr size_t staging_bytes3(bool staged) {
+  return staged ? (size_t)kChunk * 64 * sizeof(T) + 16 : 0;  // the chunk's field values and a barrier
+}
+
+template <typename T>
+constexpr size_t compress_smem3(bool staged = false) {
   using S = typename Fmt<T>::S;
-  return (size_t)chunk_buf_words3<T>() * 4 * 2  // chunk bit buffers (two components in flight)
+  return staging_bytes3<T>(staged)
+         + (size_t)chunk_buf_words3<T>() * 4 * 2  // chunk bit buffers (two components in flight)
          + (size_t)kChunk * 64 * sizeof(S)     // brick buffers, 128 elements per warp
-         + (size_t)kChunk * 64 * 8             // plane words of every brick
-         + (size_t)kChunk * 64 * 4             // plane code offsets and significance counts
+         + (planes_in_brick_buffer<T>() ? 0 : (size_t)kChunk * 64 * 8)  // plane words of every brick
+         + (planes_in_brick_buffer<T>() ? (size_t)kChunk * 64 * 4 : 0)  // plane offsets and counts
          + 2 * 32 * 4 * 4                      // per component parity: lengths, modes, escalations, violations
          + 16                                  // pool base of the two components in flight
          + 2 * 32 * 8                          // per component parity and brick: bits of max |x - x~_i|
@@ -109,9 +128,100 @@ __device__ __forceinline__ void plane_scan2(uint64_t WA, bool actA, uint64_t WB,
 // Byte m of a register of four packed shared-memory slots.
 __device__ __forceinline__ int slot_of(uint32_t packed, int m) { return (int)((packed >> (8 * m)) & 0xffu); }
 
+// Staging of a chunk's field values in shared memory with TMA (the
+// persistent construction kernel, pcz_compress.cu): when the field's rows of
+// bricks are whole chunks (bricks per row a multiple of 32), a chunk is one
+// 128x4x4 box of the field, copied with one TMA tile copy ("row" layout: value
+// (x, y, z) of the box at xs + 512 z + 128 y + x); otherwise one tile copy per
+// brick of 4x4x4 boxes ("brick" layout: brick slot j at xs + 64 j, x
+// fastest).  The copies signal an mbarrier by their bytes.  Values past the
+// field's end arrive as zeros and are never used: readers clamp to the last
+// in-field line and value (rule R4).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Waits for the barrier's phase with parity `parity` to complete, at most
+// `limit` polls (each poll may itself suspend the thread for a while); false
+// when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  const uint32_t a = smem_addr(bar);
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Issued by one thread: the copies of chunk `chunk` into xs, completing the
+// barrier's current phase.
+template <typename T>
+__device__ __forceinline__ void issue_chunk_copy(const CompressParams& P, const CUtensorMap* map, bool row_box,
+                                                 int64_t chunk, T* xs, uint64_t* bar) {
+  const int64_t b0 = chunk * kChunk;
+  const int nb = (int)(P.nbricks - b0 < kChunk ? P.nbricks - b0 : kChunk);
+  const uint32_t bytes = (uint32_t)(row_box ? kChunk : nb) * 64u * (uint32_t)sizeof(T);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  for (int j = 0; j < (row_box ? 1 : nb); ++j) {
+    const int64_t b = b0 + j;
+    const int64_t cx = b % P.nb[0], r = b / P.nb[0];
+    const int x = (int)(4 * cx), y = (int)(4 * (r % P.nb[1])), z = (int)(4 * (r / P.nb[1]));
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(smem_addr(xs + 64 * j)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+  }
+}
+
+// This lane's x-line of its brick from the staged values (R4: the nearest
+// in-field line and, along x, the last in-field value).
+template <typename T>
+__device__ __forceinline__ void staged_line(const T* xs, bool row_box, int slot, int ly, int lz, int nvx, int nvy,
+                                            int nvz, T* v) {
+  const int y = min(ly, nvy - 1), z = min(lz, nvz - 1);
+  const T* src = row_box ? xs + 512 * z + 128 * y + 4 * slot : xs + 64 * slot + 16 * z + 4 * y;
+  if (nvx == 4) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(src);
+      v[0] = a.x;
+      v[1] = a.y;
+      v[2] = a.z;
+      v[3] = a.w;
+    } else {
+      const double2 a = reinterpret_cast<const double2*>(src)[0];
+      const double2 b = reinterpret_cast<const double2*>(src)[1];
+      v[0] = a.x;
+      v[1] = a.y;
+      v[2] = b.x;
+      v[3] = b.y;
+    }
+    return;
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) v[m] = src[min(m, nvx - 1)];
+}
+
 // Algorithm 1 on every brick of index chunk `chunk` of a 3D field, all
 // components, by the whole CTA (kCompressThreads3 threads); smem holds
-// compress_smem3<T>() bytes.  Every thread of the CTA must call it.
+// compress_smem3<T>(map != nullptr) bytes, 128-byte aligned.  With a tensor
+// map, xs (= smem) holds the chunk's field values staged by TMA (row layout when
+// row_box, brick layout otherwise): each lane reads its line from there, and
+// after a CTA barrier thread 0 starts the copy of chunk `next` (if below
+// nchunks) into xs on barrier `bar`, so that it lands while this chunk is
+// coded.  Without a tensor map each lane loads its line from the field with
+// vector loads.  Every thread of the CTA must call it.
 // Copies one component's finished chunk from its shared buffer to the pool
 // (base ~0: the pool was too small) and clears the buffer for reuse.
 __device__ __forceinline__ void append_chunk(const CompressParams& P, uint32_t* buf, unsigned long long base,
@@ -125,7 +235,9 @@ __device__ __forceinline__ void append_chunk(const CompressParams& P, uint32_t* 
 }
 
 template <typename T>
-__device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t chunk, unsigned char* smem) {
+__device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t chunk, unsigned char* smem,
+                                                const CUtensorMap* map = nullptr, bool row_box = false,
+                                                uint64_t* bar = nullptr, int64_t next = -1) {
   using F = Fmt<T>;
   using U = typename F::U;
   using S = typename F::S;
@@ -141,13 +253,18 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
 
   // component i's bits go to buffer i & 1; it is appended to the pool while
   // component i + 1 is written, which saves a barrier per component
-  uint32_t* cbufs = reinterpret_cast<uint32_t*>(smem);
-  S* bbuf = reinterpret_cast<S*>(smem + (size_t)BUFW * 4 * 2);
-  uint64_t* s_pw = reinterpret_cast<uint64_t*>(bbuf + kChunk * 64);  // [warp][brick][plane] words
-  uint32_t* s_pi = reinterpret_cast<uint32_t*>(s_pw + kChunk * 64);  // [warp][brick][plane] off | n << 14 | hi << 21
+  uint32_t* cbufs = reinterpret_cast<uint32_t*>(smem + staging_bytes3<T>(map != nullptr));
+  S* bbuf = reinterpret_cast<S*>(cbufs + (size_t)BUFW * 2);
+  // [warp][brick][plane] plane words, and offsets | n << 14 | hi << 21; one of
+  // the two lives in the brick buffer
+  uint64_t* s_pw = planes_in_brick_buffer<T>() ? reinterpret_cast<uint64_t*>(bbuf)
+                                               : reinterpret_cast<uint64_t*>(bbuf + kChunk * 64);
+  uint32_t* s_pi = planes_in_brick_buffer<T>() ? reinterpret_cast<uint32_t*>(bbuf + kChunk * 64)
+                                               : reinterpret_cast<uint32_t*>(bbuf);
   // per-brick tables, one set per component parity: a warp that runs ahead
   // into component i + 1 never overwrites what slower warps still read of i
-  int* s_len = reinterpret_cast<int*>(s_pi + kChunk * 64);  // [2][32]
+  int* s_len = reinterpret_cast<int*>(planes_in_brick_buffer<T>() ? (void*)(s_pi + kChunk * 64)
+                                                                  : (void*)(s_pw + kChunk * 64));  // [2][32]
   int* s_mode = s_len + 64;
   int* s_esc = s_mode + 64;
   int* s_viol = s_esc + 64;
@@ -185,16 +302,26 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
   const bool any_partial = __any_sync(FULL, partial);
 
   T x[4], xt[4], e[4];
-  {
-    const T* field = reinterpret_cast<const T*>(P.field);
+  T* xs = reinterpret_cast<T*>(smem);
+  if (map) {
     if (have) {
-      const int64_t gy = 4 * by + min(ly, nvy - 1), gz = 4 * bz + min(lz, nvz - 1);
-      const T* row = field + (gz * P.dims[1] + gy) * P.dims[0] + 4 * bx;
-      load_line<T>(row, nvx, x);
+      staged_line<T>(xs, row_box, slot, ly, lz, nvx, nvy, nvz, x);
     } else {
 #pragma unroll
       for (int m = 0; m < 4; ++m) x[m] = T(0);
     }
+    __syncthreads();  // every lane has its values: xs is free for the next chunk
+    if (tid == 0 && next >= 0 && next < P.nchunks) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the reads above before the copy's writes
+      issue_chunk_copy<T>(P, map, row_box, next, xs, bar);
+    }
+  } else if (!have) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) x[m] = T(0);
+  } else {
+    const int64_t gy = 4 * by + min(ly, nvy - 1), gz = 4 * bz + min(lz, nvz - 1);
+    const T* row = reinterpret_cast<const T*>(P.field) + (gz * P.dims[1] + gy) * P.dims[0] + 4 * bx;
+    load_line<T>(row, nvx, x);
   }
   {
     bool bad = false;
@@ -227,6 +354,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
 
   for (int i = 0; i < P.n; ++i) {  // one component per tau_i
     uint32_t* cbuf = cbufs + (i & 1) * BUFW;
+    __syncwarp();  // the last component's plane tables (in the brick buffer) are read
     const U tb = (U)P.tau_bits[i];
     if (any_partial) {  // R4 padding of the residual
       const T last = nvx == 1 ? e[0] : nvx == 2 ? e[1] : nvx == 3 ? e[2] : e[3];

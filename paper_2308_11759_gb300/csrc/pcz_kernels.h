@@ -88,7 +88,7 @@ struct RetrieveParams {
   int pad_;
 };
 
-enum { kFlagNonFinite = 1u, kFlagPoolOverflow = 2u };
+enum { kFlagNonFinite = 1u, kFlagPoolOverflow = 2u, kFlagStageTimeout = 4u };
 
 // Batched construction: one persistent launch over the chunks of many
 // fields.  The work list is implicit: slot s (schedule order) covers field
@@ -125,7 +125,9 @@ struct ScanParams {
 };
 
 // Launchers (each returns the launch error).
-cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaStream_t s);
+// device_field: the field is device memory (not host memory mapped into the
+// device), so the 3D kernel may stage its bricks with TMA tile copies.
+cudaError_t launch_compress(int dtype, int ndims, const CompressParams& p, cudaStream_t s, bool device_field = false);
 cudaError_t launch_retrieve(int dtype, int ndims, const RetrieveParams& p, cudaStream_t s);
 // 1D and 2D fields (one thread per brick); called by the two above.
 cudaError_t launch_compress_small(int dtype, int ndims, const CompressParams& p, cudaStream_t s);
