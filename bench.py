@@ -50,16 +50,21 @@ sys.path.insert(0, ROOT)
 
 N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
-# DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
-# capture of the current kernels.
-TRAFFIC = {"retrieve": 1140515275}
-TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 16 retrieval launches of "
-                  "the 320^3 case, scaled by the bricks processed to 512^3")
-# Pipe utilisation of the retrieval kernel (ncu --set full, k = 8 launch of the 320^3 case of
-# this workload, current kernels): it is bound by integer issue, not by HBM.
-PIPES = {"kernel": "retrieve", "launch": "k = 8, 320^3",
-         "alu": {"f32": 0.570, "f64": 0.574}, "fp64": {"f32": 0.0, "f64": 0.662},
-         "issue_active": {"f32": 0.678, "f64": 0.605},
+# DRAM bytes (read + write) and warp instructions per launch of the dominant kernel on this
+# workload, means over the 16 retrieval launches of a step (k = 1..8, float32 and float64), from
+# one ncu capture of the current kernels at 512^3 (gpu__time_duration, dram__bytes_read/write,
+# smsp__inst_executed: one pass).
+TRAFFIC = {"retrieve": 1291889936}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over the 16 retrieval launches "
+                  "(k = 1..8, float32 and float64) of this workload at 512^3")
+INSTRUCTIONS = {"retrieve": 2051047084}
+# Pipe utilisation (ncu --set full on the 320^3 case of this workload, current kernels): the
+# retrieval (k = 8) and compression kernels are bound by instruction issue, not by HBM.
+PIPES = {"launch": "320^3, retrieval at k = 8, compression of 8 components",
+         "retrieve": {"alu": {"f32": 0.569, "f64": 0.574}, "fp64": {"f32": 0.0, "f64": 0.662},
+                      "issue_active": {"f32": 0.677, "f64": 0.604}},
+         "compress": {"alu": {"f32": 0.708, "f64": 0.598}, "fp64": {"f32": 0.0, "f64": 0.464},
+                      "issue_active": {"f32": 0.762, "f64": 0.584}},
          "source": "ncu sm__inst_executed_pipe_{alu,fp64}.avg.pct_of_peak_sustained_active, "
                    "smsp__issue_active.avg.pct_of_peak_sustained_active"}
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
@@ -136,6 +141,22 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(mhz)}
+
+
+def issue_roofline(kernel, ms_per_launch, clocks):
+    """The bound the kernels actually sit on: warp instructions issued per second
+    (the kernel's instructions per launch from the ncu capture, over its live
+    CUDA-event duration) against the SMs' issue peak, 152 SMs x 4 schedulers x one
+    warp instruction per clock, at the median SM clock sampled in the timed region."""
+    inst = INSTRUCTIONS.get(kernel)
+    if not inst or ms_per_launch <= 0:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    achieved = inst / (ms_per_launch * 1e-3)
+    peak = 152 * 4 * mhz * 1e6
+    return {"achieved": round(achieved / 1e9, 1), "peak": round(peak / 1e9, 1), "unit": "G warp-instructions/s",
+            "frac": round(achieved / peak, 4), "sm_mhz": mhz,
+            "instructions_per_launch": inst, "source": "ncu smsp__inst_executed.sum, mean over the same 16 launches"}
 
 
 def max_over_ranks(ms, world, device):
@@ -378,7 +399,8 @@ def run_pcz(args, rank, world, device):
                           "traffic": TRAFFIC.get(dom),
                           "traffic_source": TRAFFIC_SOURCE if TRAFFIC.get(dom) else None,
                           "algorithmic_bytes_per_launch": int(alg[dom] / max(dom_n, 1)),
-                          "ms_per_launch": round(dom_ms / max(dom_n, 1), 4)},
+                          "ms_per_launch": round(dom_ms / max(dom_n, 1), 4),
+                          "issue": issue_roofline(dom, dom_ms / max(dom_n, 1), clocks)},
                 e2e=e2e, fields=fields)
 
 
