@@ -370,24 +370,25 @@ def run_pcz(args, rank, world, device):
         for name, x in fields.items():
             hbufs[name] = x.cpu().pin_memory()
             hbufs[name + "_out"] = torch.empty(x.shape, dtype=x.dtype).pin_memory()
-        step(host=True, hbufs=hbufs)
+        for _ in range(args.warmup):
+            step(host=True, hbufs=hbufs)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         a = time.perf_counter()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        marks[0].record()
+        for i in range(args.steps):
             step(host=True, hbufs=hbufs)
-        e1.record()
+            marks[i + 1].record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - a
-        ems = max_over_ranks(e0.elapsed_time(e1), world, device)
+        ems = max_over_ranks(marks[0].elapsed_time(marks[-1]), world, device)
         h2d = sum(v["field_bytes"] for v in info.values())
         d2h = sum(v["field_bytes"] * N_COMP for v in info.values())
         e2e = {"value": round(job_gbs(world, raw_bytes_step, args.steps, ems), 3), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems / args.steps, 3),
+               "ms_steps": [round(marks[i].elapsed_time(marks[i + 1]), 2) for i in range(args.steps)],
                "host_wall_s": round(wall, 3)}
     for st in held.values():
         st.close()

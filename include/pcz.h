@@ -20,7 +20,13 @@
  *    pointers are accepted where stated: pinned (page-locked) host memory is
  *    read or written in place by the kernels through its device mapping (on
  *    a Grace-Blackwell node over the C2C link, overlapped with the
- *    computation); pageable host memory is copied through the same stream.
+ *    computation), except that a retrieval output of 32 MiB or more in
+ *    pinned memory is decoded into device staging slabs of whole brick
+ *    layers that the copy engines move to the host while the next slab
+ *    decodes.  Results in pinned host memory are complete in stream order,
+ *    as after a cudaMemcpyAsync: synchronise cuda_stream before reading them.
+ *    Pageable host memory is copied through the same stream, and such calls
+ *    return with the data in place.
  *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
  *    are asynchronous on it except where they must read a result back.
  *  - The caller owns its input and output buffers.  The library owns the

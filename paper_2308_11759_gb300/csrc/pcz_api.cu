@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -596,6 +597,83 @@ pc_status pc_query_k(const pc_streams* s, double tau, int* k_out) {
   return fail(PC_ERR_TOL_UNREACHABLE, "tolerance finer than the last component's");
 }
 
+// A per-device stream of the library for copies between the device and
+// pinned host memory, so that they overlap the kernels of the caller's stream.
+static cudaStream_t copy_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  cudaStream_t& cs = streams[dev & 127];
+  if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cs = nullptr;
+  }
+  return cs;
+}
+
+// Retrieval into pinned host memory by slabs of whole brick layers along z:
+// each slab is decoded into one of two device staging buffers on the caller's
+// stream, and the copy engines move it to the host on the library's copy
+// stream while the next slab decodes (a slab of the box is a contiguous run of
+// its bytes, x fastest).  With read_in (refinement) each slab's x~_k0 is first
+// copied in.  The caller's stream waits for the last copy, so the host buffer
+// is complete in stream order, as after a cudaMemcpyAsync.
+static pc_status retrieve_pinned_slabs(const pc_streams* s, int k0, int k, const int64_t lo[3], const int64_t hi[3],
+                                       char* hbuf, int read_in, cudaStream_t st, cudaStream_t cs) {
+  const size_t T = dsize(s->dtype);
+  const size_t plane = (size_t)((hi[0] - lo[0]) * (hi[1] - lo[1])) * T;  // bytes of one z-plane of the box
+  constexpr size_t kSlabTarget = size_t(64) << 20;
+  int64_t layers = (int64_t)(kSlabTarget / (4 * plane));  // brick layers (4 planes) per slab
+  if (layers < 1) layers = 1;
+  // slab boundaries on brick layers (z multiple of 4), the box's own ends excepted
+  std::vector<int64_t> zs{lo[2]};
+  while (zs.back() < hi[2]) {
+    const int64_t z = zs.back();
+    const int64_t next = std::min(hi[2], (z / 4 + layers) * 4);
+    zs.push_back(next);
+  }
+  const int nslab = (int)zs.size() - 1;
+  size_t max_bytes = 0;
+  for (int i = 0; i < nslab; ++i) max_bytes = std::max(max_bytes, (size_t)(zs[i + 1] - zs[i]) * plane);
+  Scratch scr(st);
+  void* stage[2] = {nullptr, nullptr};
+  CK(scr.get(&stage[0], max_bytes));
+  CK(scr.get(&stage[1], max_bytes));
+  cudaEvent_t kdone[2] = {nullptr, nullptr}, cdone[2] = {nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+    e = cudaEventCreateWithFlags(&kdone[j], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&cdone[j], cudaEventDisableTiming);
+  }
+  pc_status r = PC_OK;
+  for (int i = 0; i < nslab && e == cudaSuccess && r == PC_OK; ++i) {
+    const int b = i & 1;
+    int64_t slo[3] = {lo[0], lo[1], zs[i]}, shi[3] = {hi[0], hi[1], zs[i + 1]};
+    const size_t off = (size_t)(zs[i] - lo[2]) * plane, bytes = (size_t)(zs[i + 1] - zs[i]) * plane;
+    if (i >= 2) e = cudaStreamWaitEvent(st, cdone[b], 0);  // staging buffer b has been copied out
+    if (e == cudaSuccess && read_in) e = cudaMemcpyAsync(stage[b], hbuf + off, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) break;
+    r = run_retrieve(s, k0, k, slo, shi, stage[b], 1, st);
+    if (r != PC_OK) break;
+    e = cudaEventRecord(kdone[b], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, kdone[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hbuf + off, stage[b], bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(cdone[b], cs);
+  }
+  // the caller's stream (and the staging buffers' release on it) wait for every copy
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+    if (j < nslab) e = cudaStreamWaitEvent(st, cdone[j], 0);
+  for (int j = 0; j < 2; ++j) {
+    if (kdone[j]) cudaEventDestroy(kdone[j]);
+    if (cdone[j]) cudaEventDestroy(cdone[j]);
+  }
+  if (r != PC_OK) return r;
+  CK(e);
+  return PC_OK;
+}
+
 static pc_status retrieve_common(const pc_streams* s, int k0, int k, const pc_box* box, void* buf, int read_in,
                                  void* cuda_stream) {
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -605,10 +683,14 @@ static pc_status retrieve_common(const pc_streams* s, int k0, int k, const pc_bo
   const size_t bytes = (size_t)((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])) * dsize(s->dtype);
   const void* kp = nullptr;
   bool host = false;
-  if (kernel_pointer(buf, &kp, &host)) {  // device memory, or pinned host memory written in place
-    r = run_retrieve(s, k0, k, lo, hi, const_cast<void*>(kp), 1, st);
-    if (r == PC_OK && host) CK(cudaStreamSynchronize(st));
-    return r;
+  if (kernel_pointer(buf, &kp, &host)) {
+    if (host && s->ndims == 3 && k > k0 && bytes >= (size_t(32) << 20)) {
+      // a large box in pinned host memory: decoded into device slabs and copied by the copy engines
+      cudaStream_t cs = copy_stream();
+      if (cs) return retrieve_pinned_slabs(s, k0, k, lo, hi, static_cast<char*>(buf), read_in, st, cs);
+    }
+    // device memory, or pinned host memory written in place by the kernel
+    return run_retrieve(s, k0, k, lo, hi, const_cast<void*>(kp), 1, st);
   }
   Scratch scr(st);
   void* d = nullptr;

@@ -194,3 +194,31 @@ def test_lossless_sweep(P):
         assert r["bits_per_value"] == bits and r["ratio"] == 8 * x.itemsize / bits
         ref = O.Streams(x, [st.tau(i) for i in range(st.n)], nthreads=4)
         assert [ref.measured(i) for i in range(st.n)] == r["measured"]
+
+
+def test_pinned_output_by_slabs(P):
+    """A retrieval of 32 MiB or more into pinned host memory goes through device
+    staging slabs of whole brick layers (about 64 MiB each) and the copy
+    engines: a 320x256x258 float64 field (169 MB, three slabs, so each staging
+    buffer is reused).  The result, read after the stream is synchronised,
+    equals the device retrieval for the full box, for a sub-box whose first
+    slab starts inside a brick layer, and for a refinement read from and
+    written to pinned memory."""
+    x = S.powerlaw((320, 256, 258), seed=44, dtype=np.float64)
+    tau = O.tau_decade(O.value_range(x), 6)
+    st = P.compress(torch.from_numpy(x).cuda(), tau)
+    for k in (1, 6):
+        out = torch.empty(x.shape, dtype=torch.float64).pin_memory()
+        st.retrieve(k=k, out=out)
+        torch.cuda.synchronize()
+        assert torch.equal(out.view(torch.uint8), st.retrieve(k=k).cpu().view(torch.uint8))
+    box = ([3, 1, 2], [317, 256, 257])
+    part = torch.empty((314, 255, 255), dtype=torch.float64).pin_memory()
+    st.retrieve(k=4, box=box, out=part)
+    torch.cuda.synchronize()
+    assert torch.equal(part.view(torch.uint8), st.retrieve(k=4, box=box).cpu().view(torch.uint8))
+    acc = torch.empty(x.shape, dtype=torch.float64).pin_memory()
+    st.retrieve(k=2, out=acc)
+    st.refine(2, 5, acc)
+    torch.cuda.synchronize()
+    assert torch.equal(acc.view(torch.uint8), st.retrieve(k=5).cpu().view(torch.uint8))
