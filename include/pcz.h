@@ -30,7 +30,10 @@
  *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
  *    are asynchronous on it except where they must read a result back.
  *  - The caller owns its input and output buffers.  The library owns the
- *    component streams (device memory) until pc_streams_free.
+ *    component streams (device memory) until pc_streams_free.  Device memory
+ *    the library frees (streams, scratch) stays in a stream-ordered pool of
+ *    its own for later calls, so that steady-state calls map no new memory;
+ *    pc_release_cached_memory hands it back to the driver.
  *  - No C++ exception crosses this interface.  Every call returns a pc_status;
  *    pc_last_error() gives a message for the last failure on this thread.
  *  - Not thread-safe on one pc_streams object; different objects may be used
@@ -179,6 +182,15 @@ pc_status pc_stream_read(const pc_streams *s, int i, uint64_t word_off, uint64_t
 
 /* Releases the streams and their device memory (waits for the device). */
 void pc_streams_free(pc_streams *s);
+
+/*
+ * Returns the device memory the library keeps for later calls -- freed
+ * streams and scratch in its pools, and the bit pool of the construction
+ * kernel -- to the driver, on every device the library has used.  Waits for
+ * each such device first.  Live pc_streams are untouched.  Not to be called
+ * while another thread is inside a library call.
+ */
+pc_status pc_release_cached_memory(void);
 
 /*
  * The range min/max of a field in device or pinned host memory (Sec. 5.1:

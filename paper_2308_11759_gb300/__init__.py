@@ -117,6 +117,8 @@ def lib():
         L.pc_streams_free.restype = None
         L.pc_last_error.argtypes = []
         L.pc_last_error.restype = C.c_char_p
+        L.pc_release_cached_memory.argtypes = []
+        L.pc_release_cached_memory.restype = C.c_int
         L.pc_version.argtypes = []
         L.pc_version.restype = C.c_int
         _lib = L
@@ -577,6 +579,12 @@ def debug_status(reset: bool = False):
 
 
 KERNEL_KINDS = ("compress", "scan", "pack", "retrieve", "range")
+
+
+def release_cached_memory():
+    """Returns the device memory the library keeps for later calls (freed
+    streams, scratch, the construction bit pool) to the driver."""
+    _check(lib().pc_release_cached_memory())
 
 
 def timing_enable(on: bool = True):

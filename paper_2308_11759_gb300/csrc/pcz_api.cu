@@ -235,19 +235,28 @@ void pcz::set_last_error(const char* msg) { g_err = msg; }
 
 namespace {
 
+// The device arrays of a pc_streams come from the library's memory pool (on
+// the stream of the call that makes them, which synchronises before it
+// returns), so that neither making nor releasing streams maps or unmaps device
+// memory.  Release waits for the device first: work on any stream may still
+// read the arrays; then their memory goes back to the pool at once.
 void streams_release(pc_streams* s) {
   if (!s) return;
   cudaDeviceSynchronize();
   if (!s->backing) {  // a batch's streams share device arenas, freed with the last of them
-    cudaFree(s->d_payload);
-    cudaFree(s->d_chunk_word);
-    cudaFree(s->d_brick_len);
-    cudaFree(s->d_brick_off);
-    cudaFree(s->d_desc);
-    cudaFree(s->d_err);
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != s->device) cudaSetDevice(s->device);
+    void* arrays[] = {s->d_payload, s->d_chunk_word, s->d_brick_len, s->d_brick_off, s->d_desc, s->d_err};
+    for (void* a : arrays)
+      if (a) cudaFreeAsync(a, 0);
+    if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
   }
   delete s;
 }
+
+// One device array of a pc_streams, from the library's pool on stream st.
+cudaError_t streams_alloc(void** p, size_t bytes, cudaStream_t st) { return scratch_alloc(p, bytes, st); }
 
 // Uploads the per-component descriptors the retrieval kernel reads.
 pc_status upload_desc(pc_streams* s, cudaStream_t st) {
@@ -466,11 +475,11 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
     SCR(used, 16);
     SCR(comp_base, 8 * n);
 #undef SCR
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_desc, sizeof(CompDesc) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 16);
+    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16, st);
+    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16, st);
+    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16, st);
+    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_desc, sizeof(CompDesc) * n, st);
+    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_err, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
     if (e != cudaSuccess) {
       streams_release(s);
@@ -548,7 +557,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
         for (int k = 0; k < 5; ++k) s->counts[i][k] = h_cnt[5 * i + k];
         s->measured[i] = bits_to_double(h_merr[i], dtype);
       }
-      e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
+      e = streams_alloc((void**)&s->d_payload, 8 * total + 16, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(comp_base, base.data(), 8 * n, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) {
         TimedLaunch tl(PC_KERNEL_PACK, st);
@@ -904,12 +913,12 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   s->device = dev;
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_payload, 8 * total + 16);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_desc, sizeof(CompDesc) * n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_err, 16);
+  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_payload, 8 * total + 16, st);
+  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16, st);
+  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16, st);
+  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16, st);
+  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_desc, sizeof(CompDesc) * n, st);
+  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_err, 16, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     e = cudaMemcpyAsync(s->d_chunk_word + (int64_t)i * nch, p + off, 8 * nch, cudaMemcpyHostToDevice, st);
@@ -973,6 +982,31 @@ pc_status pc_stream_read(const pc_streams* s, int i, uint64_t word_off, uint64_t
 }
 
 void pc_streams_free(pc_streams* s) { streams_release(s); }
+
+pc_status pc_release_cached_memory(void) {
+  g_err.clear();
+  int cur = 0;
+  CK(cudaGetDevice(&cur));
+  cudaError_t e = cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_mu);  // the construction bit pools
+  std::lock_guard<std::mutex> lp(g_pool_mu);
+  for (int dev = 0; dev < 128; ++dev) {
+    if (!g_pools[dev] && !g_ctx[dev].pool) continue;
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) break;
+    if (g_ctx[dev].pool) {
+      e = cudaFree(g_ctx[dev].pool);
+      g_ctx[dev].pool = nullptr;
+      g_ctx[dev].pool_words = 0;
+    }
+    if (e == cudaSuccess && g_pools[dev]) e = cudaMemPoolTrimTo(g_pools[dev], 0);
+  }
+  const cudaError_t e2 = cudaSetDevice(cur);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "pc_release_cached_memory");
+  return PC_OK;
+}
 
 pc_status pc_timing_enable(int on) {
   g_err.clear();
