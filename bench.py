@@ -586,7 +586,8 @@ def run_batched(args, device):
                                         "(two kernels); one kernel for both with 1 or 2 chunks per warp; two items "
                                         "per claim or the fields in the given order for 3 shapes",
                           "candidate_ms": [round(v, 3) for v in info["candidate_ms"]],
-                          "spread": round(max(info["candidate_ms"]) / min(info["candidate_ms"]) - 1.0, 4),
+                          "spread": round(max(v for v in info["candidate_ms"] if v > 0)
+                                          / min(v for v in info["candidate_ms"] if v > 0) - 1.0, 4),
                           "first_call_s": round(t_tune, 3)},
             "graph": bool(info["graph"]), "timing": "CUDA events around whole calls (host work included)",
             "oracle": oracle}

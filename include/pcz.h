@@ -414,8 +414,11 @@ pc_status pc_server_free(pc_server *srv);
  * the 3D kernel (1 at up to 128 registers per thread, or 2 at 64), warps per
  * CTA of the 1D/2D kernel (2 to 16), chunks per warp in a 1D/2D work item
  * (1 or 2), items per claim (1 or 2), or instead one kernel of 16-warp CTAs
- * that takes the items of both parts from one queue.  The result of every call is exactly what pc_compress
- * gives for each field on its own, bit for bit.
+ * that takes the items of both parts from one queue.  For float64 the
+ * schedules with 16-warp 1D/2D CTAs and the single kernel are left out (their
+ * 128 registers per thread are too few for a 2D float64 brick).  The result
+ * of every call is exactly what pc_compress gives for each field on its own,
+ * bit for bit.
  *
  *   pc_batch_create: nfields >= 1; dims: 3 extents per field (x first,
  *     entries beyond the field's ndims ignored); ndims: 1..3 per field; n
@@ -442,7 +445,7 @@ typedef struct {
   int warps_small;       /* warps per CTA of the 1D/2D kernel (2, 4, 8 or 16) */
   int mixed;             /* 1 when one kernel codes both parts from one queue */
   uint64_t calls;        /* pc_batch_compress calls so far */
-  double candidate_ms[16]; /* the autotuner's timings (ms) */
+  double candidate_ms[16]; /* the autotuner's timings (ms); -1: not a schedule of this type */
 } pc_batch_info_t;
 
 pc_status pc_batch_create(int nfields, const int64_t *dims, const int *ndims, pc_dtype dtype, int n,

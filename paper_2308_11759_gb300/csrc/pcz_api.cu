@@ -57,36 +57,43 @@ std::mutex g_mu;
 DevCtx g_ctx[128];
 
 std::mutex g_pool_mu;
-cudaMemPool_t g_pools[128] = {};
+// [0]: scratch and the streams' index arrays; [1]: the streams' payloads.
+// Payloads have a pool of their own so that the smaller arrays never split
+// a freed payload block: a payload of the size freed before is then served
+// from that block without mapping new memory.
+cudaMemPool_t g_pools[2][128] = {};
 
-}  // namespace
-
-// The library's own stream-ordered memory pool on the current device.  It
+// The library's stream-ordered memory pool `which` on the current device.  It
 // keeps freed memory for later calls: the device's default pool hands it back
 // to the driver at every synchronisation, so that the next call would pay
 // for fresh allocations again.
-cudaError_t pcz::scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+cudaError_t pool_alloc(int which, void** p, size_t bytes, cudaStream_t st) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   cudaMemPool_t pool = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_pool_mu);
-    if (!g_pools[dev & 127]) {
+    cudaMemPool_t& slot = g_pools[which][dev & 127];
+    if (!slot) {
       cudaMemPoolProps props;
       std::memset(&props, 0, sizeof(props));
       props.allocType = cudaMemAllocationTypePinned;
       props.location.type = cudaMemLocationTypeDevice;
       props.location.id = dev;
-      e = cudaMemPoolCreate(&g_pools[dev & 127], &props);
+      e = cudaMemPoolCreate(&slot, &props);
       if (e != cudaSuccess) return e;
       uint64_t keep = ~0ull;
-      cudaMemPoolSetAttribute(g_pools[dev & 127], cudaMemPoolAttrReleaseThreshold, &keep);
+      cudaMemPoolSetAttribute(slot, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    pool = g_pools[dev & 127];
+    pool = slot;
   }
   return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
+
+}  // namespace
+
+cudaError_t pcz::scratch_alloc(void** p, size_t bytes, cudaStream_t st) { return pool_alloc(0, p, bytes, st); }
 
 namespace {
 
@@ -256,7 +263,8 @@ void streams_release(pc_streams* s) {
 }
 
 // One device array of a pc_streams, from the library's pool on stream st.
-cudaError_t streams_alloc(void** p, size_t bytes, cudaStream_t st) { return scratch_alloc(p, bytes, st); }
+cudaError_t streams_alloc(void** p, size_t bytes, cudaStream_t st) { return pool_alloc(0, p, bytes, st); }
+cudaError_t payload_alloc(void** p, size_t bytes, cudaStream_t st) { return pool_alloc(1, p, bytes, st); }
 
 // Uploads the per-component descriptors the retrieval kernel reads.
 pc_status upload_desc(pc_streams* s, cudaStream_t st) {
@@ -557,7 +565,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
         for (int k = 0; k < 5; ++k) s->counts[i][k] = h_cnt[5 * i + k];
         s->measured[i] = bits_to_double(h_merr[i], dtype);
       }
-      e = streams_alloc((void**)&s->d_payload, 8 * total + 16, st);
+      e = payload_alloc((void**)&s->d_payload, 8 * total + 16, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(comp_base, base.data(), 8 * n, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) {
         TimedLaunch tl(PC_KERNEL_PACK, st);
@@ -913,7 +921,7 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   s->device = dev;
-  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_payload, 8 * total + 16, st);
+  if (e == cudaSuccess) e = payload_alloc((void**)&s->d_payload, 8 * total + 16, st);
   if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16, st);
   if (e == cudaSuccess) e = streams_alloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16, st);
   if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16, st);
@@ -991,7 +999,7 @@ pc_status pc_release_cached_memory(void) {
   std::lock_guard<std::mutex> lk(g_mu);  // the construction bit pools
   std::lock_guard<std::mutex> lp(g_pool_mu);
   for (int dev = 0; dev < 128; ++dev) {
-    if (!g_pools[dev] && !g_ctx[dev].pool) continue;
+    if (!g_pools[0][dev] && !g_pools[1][dev] && !g_ctx[dev].pool) continue;
     if (e == cudaSuccess) e = cudaSetDevice(dev);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) break;
@@ -1000,7 +1008,8 @@ pc_status pc_release_cached_memory(void) {
       g_ctx[dev].pool = nullptr;
       g_ctx[dev].pool_words = 0;
     }
-    if (e == cudaSuccess && g_pools[dev]) e = cudaMemPoolTrimTo(g_pools[dev], 0);
+    for (int w = 0; w < 2; ++w)
+      if (e == cudaSuccess && g_pools[w][dev]) e = cudaMemPoolTrimTo(g_pools[w][dev], 0);
   }
   const cudaError_t e2 = cudaSetDevice(cur);
   if (e == cudaSuccess) e = e2;

@@ -236,13 +236,14 @@ static int batch_mixed_grid_t() {
   return grid;
 }
 
-int compress_batch_mixed_grid(int dtype) { return dtype == 1 ? batch_mixed_grid_t<float>() : batch_mixed_grid_t<double>(); }
+// The mixed kernel exists for float32 only: its CTAs of 16 warps hold a
+// thread to 128 registers, and a 2D float64 brick coded in one thread's
+// registers needs more (it would spill about 2 KB per thread).
+int compress_batch_mixed_grid(int dtype) { return dtype == 1 ? batch_mixed_grid_t<float>() : 0; }
 
 cudaError_t launch_compress_batch_mixed(int dtype, const BatchParams* d_bp, int grid, cudaStream_t s) {
-  if (dtype == 1)
-    k_batch_mixed<float><<<grid, kCompressThreads3, batch_mixed_smem<float>(), s>>>(d_bp);
-  else
-    k_batch_mixed<double><<<grid, kCompressThreads3, batch_mixed_smem<double>(), s>>>(d_bp);
+  if (dtype != 1) return cudaErrorNotSupported;
+  k_batch_mixed<float><<<grid, kCompressThreads3, batch_mixed_smem<float>(), s>>>(d_bp);
   return cudaGetLastError();
 }
 
@@ -297,7 +298,7 @@ int compress_batch_small_grid(int dtype, int warps) {
   return warps == 2   ? batch_small_grid_t<double, 2>()
          : warps == 4 ? batch_small_grid_t<double, 4>()
          : warps == 8 ? batch_small_grid_t<double, 8>()
-                      : batch_small_grid_t<double, 16>();
+                      : 0;  // no 16-warp float64 variant (see launch_small_t)
 }
 
 cudaError_t launch_compress_batch(int dtype, int minb, const BatchParams* d_bp, int grid, cudaStream_t s) {
@@ -315,24 +316,27 @@ cudaError_t launch_compress_batch(int dtype, int minb, const BatchParams* d_bp, 
   return cudaGetLastError();
 }
 
+// CTAs of 16 warps exist for float32 only: 512 threads leave 128 registers a
+// thread, fewer than a 2D float64 brick in one thread's registers takes.
 template <typename T>
-static void launch_small_t(int warps, const BatchParams* d_bp, int grid, cudaStream_t s) {
-  if (warps == 2)
+static cudaError_t launch_small_t(int warps, const BatchParams* d_bp, int grid, cudaStream_t s) {
+  if (warps == 2) {
     k_batch_small<T, 2><<<grid, 64, batch_small_smem<T, 2>(), s>>>(d_bp);
-  else if (warps == 4)
+  } else if (warps == 4) {
     k_batch_small<T, 4><<<grid, 128, batch_small_smem<T, 4>(), s>>>(d_bp);
-  else if (warps == 8)
+  } else if (warps == 8) {
     k_batch_small<T, 8><<<grid, 256, batch_small_smem<T, 8>(), s>>>(d_bp);
-  else
-    k_batch_small<T, 16><<<grid, 512, batch_small_smem<T, 16>(), s>>>(d_bp);
+  } else {
+    if constexpr (sizeof(T) == 4)
+      k_batch_small<T, 16><<<grid, 512, batch_small_smem<T, 16>(), s>>>(d_bp);
+    else
+      return cudaErrorNotSupported;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_compress_batch_small(int dtype, int warps, const BatchParams* d_bp, int grid, cudaStream_t s) {
-  if (dtype == 1)
-    launch_small_t<float>(warps, d_bp, grid, s);
-  else
-    launch_small_t<double>(warps, d_bp, grid, s);
-  return cudaGetLastError();
+  return dtype == 1 ? launch_small_t<float>(warps, d_bp, grid, s) : launch_small_t<double>(warps, d_bp, grid, s);
 }
 
 }  // namespace pcz
@@ -390,6 +394,13 @@ int variant_of(const Schedule& sc) {
   const int w = sc.warps_small == 2 ? 0 : sc.warps_small == 4 ? 1 : sc.warps_small == 8 ? 2 : 3;
   return (sc.ctas3 - 1) * 4 + w;
 }
+
+// Kernel variants that exist for the type: float64 has neither 16-warp 1D/2D
+// CTAs nor the mixed kernel (both would hold a thread to 128 registers).
+bool variant_exists(int v, pc_dtype dt) {
+  return dt == PC_F32 || (v != kVariants - 1 && kSmallShapes[v % 4] != 16);
+}
+bool schedule_exists(const Schedule& sc, pc_dtype dt) { return variant_exists(variant_of(sc), dt); }
 
 }  // namespace
 
@@ -735,7 +746,8 @@ pc_status pc_batch_create(int nfields, const int64_t* dims, const int* ndims, pc
   sp.seg_len = B->d_seg_len;
   sp.nseg = B->nseg;
   pc_status r = PC_OK;
-  for (int v = 0; v < kVariants && r == PC_OK; ++v) r = capture_graph(B, v);
+  for (int v = 0; v < kVariants && r == PC_OK; ++v)
+    if (variant_exists(v, B->dtype)) r = capture_graph(B, v);
   if (r != PC_OK) {
     batch_release(B);
     return r;
@@ -805,6 +817,10 @@ pc_status pc_batch_compress(pc_batch* B, const void* const* d_fields, const doub
     BK(cudaEventCreate(&b));
     double best = 1e30;
     for (int c = 0; c < kNumSchedules; ++c) {
+      if (!schedule_exists(kSchedules[c], B->dtype)) {
+        B->tune_ms[c] = -1.0;  // not a schedule of this type
+        continue;
+      }
       set_schedule(B, kSchedules[c]);
       pc_status r = run_graph(B, &flags);  // also sizes the pool
       if (r != PC_OK) return r;

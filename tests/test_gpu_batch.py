@@ -65,7 +65,12 @@ def test_batch_equals_alone_and_replays(P, dtype):
     info = plan.info()
     assert info["graph"] == 1 and info["calls"] == 1
     assert 0 <= info["schedule"] < info["candidates"]
-    assert all(ms > 0 for ms in info["candidate_ms"])
+    timed = [ms for ms in info["candidate_ms"] if ms != -1.0]
+    assert all(ms > 0 for ms in timed)
+    # float64 has no 16-warp 1D/2D or mixed schedule (128 registers a thread
+    # are too few for a 2D float64 brick): 9 of the 16 schedules remain
+    assert len(timed) == (16 if dtype == np.float32 else 9)
+    assert info["candidate_ms"][info["schedule"]] > 0
     # the same plan, new values and tolerances: the graph replays with new parameters
     xs2 = _fields(dtype, 90)
     taus2 = _taus(xs2, n, 1)
