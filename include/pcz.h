@@ -161,7 +161,9 @@ pc_status pc_streams_deserialize(const void *h_buf, size_t len, void *cuda_strea
 
 /* Device pointers of component i's data (for users that move components
  * between memories themselves, Sec. 6.2): payload (u64 words), chunk word
- * offsets (u64 per 32 bricks) and brick bit lengths (u16 per brick). */
+ * offsets (u64 per 32 bricks) and brick bit lengths (u16 per brick).  They
+ * stay valid until pc_streams_free, which does not wait for the caller's own
+ * work on them. */
 pc_status pc_stream_device_ptrs(const pc_streams *s, int i, const uint64_t **payload, const uint64_t **chunk_word,
                                 const uint16_t **brick_len, uint64_t *payload_words, uint64_t *nchunks,
                                 uint64_t *nbricks);
@@ -180,7 +182,10 @@ pc_status pc_stream_read_index(const pc_streams *s, int i, uint64_t *h_chunk_wor
 pc_status pc_stream_read(const pc_streams *s, int i, uint64_t word_off, uint64_t nwords, uint64_t *h_out,
                          void *cuda_stream);
 
-/* Releases the streams and their device memory (waits for the device). */
+/* Releases the streams and their device memory.  Waits for the library's
+ * launches that read them (retrievals and refinements on any stream), not for
+ * the rest of the device; work the caller launched on the arrays of
+ * pc_stream_device_ptrs must have finished.  NULL is a no-op. */
 void pc_streams_free(pc_streams *s);
 
 /*

@@ -113,8 +113,23 @@ struct Scratch {
   }
 };
 
+// Makes the current device's primary context current on this host thread
+// (once per thread): a thread whose first CUDA call is a pointer query would
+// otherwise see pinned host memory as unregistered.
+void bind_context() {
+  thread_local bool bound = false;
+  if (bound) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();  // this call's own failure; the query below reports what it finds
+    return;
+  }
+  bound = true;
+}
+
 // Where a caller's pointer lives.
 bool is_device_ptr(const void* p) {
+  bind_context();
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -128,6 +143,7 @@ bool is_device_ptr(const void* p) {
 // Grace-Blackwell node the kernels then read and write it over the C2C link,
 // so the transfer overlaps the computation).  False for pageable memory.
 bool kernel_pointer(const void* p, const void** dptr, bool* host) {
+  bind_context();
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -242,23 +258,56 @@ void pcz::set_last_error(const char* msg) { g_err = msg; }
 
 namespace {
 
-// The device arrays of a pc_streams come from the library's memory pool (on
+// A stream of the library's own on the current device (non-blocking, made
+// once): 0 for the copies of retrievals into pinned memory, 1 for releases.
+cudaStream_t lib_stream(int which) {
+  static std::mutex mu;
+  static cudaStream_t streams[2][128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  cudaStream_t& cs = streams[which][dev & 127];
+  if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cs = nullptr;
+  }
+  return cs;
+}
+
+// The device arrays of a pc_streams come from the library's memory pools (on
 // the stream of the call that makes them, which synchronises before it
 // returns), so that neither making nor releasing streams maps or unmaps device
-// memory.  Release waits for the device first: work on any stream may still
-// read the arrays; then their memory goes back to the pool at once.
-void streams_release(pc_streams* s) {
+// memory.  Release waits for the library's launches that read the arrays --
+// on whatever streams they were queued -- and not for the rest of the device,
+// so that a thread freeing its streams does not stall work other threads have
+// queued; the memory is back in the pool when it returns.  sync_device (the
+// error paths of the calls that make streams, whose allocations may still be
+// pending on their stream) waits for the device first.
+void streams_release(pc_streams* s, bool sync_device = false) {
   if (!s) return;
-  cudaDeviceSynchronize();
-  if (!s->backing) {  // a batch's streams share device arenas, freed with the last of them
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (cur != s->device) cudaSetDevice(s->device);
-    void* arrays[] = {s->d_payload, s->d_chunk_word, s->d_brick_len, s->d_brick_off, s->d_desc, s->d_err};
-    for (void* a : arrays)
-      if (a) cudaFreeAsync(a, 0);
-    if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
+  if (s->backing) {  // a batch's streams share device arenas, freed with the last of them
+    cudaDeviceSynchronize();
+    delete s;
+    return;
   }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != s->device) cudaSetDevice(s->device);
+  cudaStream_t rs = lib_stream(1);
+  {
+    std::lock_guard<std::mutex> lk(s->use_mu);
+    if (sync_device || s->sync_device || !rs) cudaDeviceSynchronize();
+    for (auto& u : s->uses) {
+      if (rs) cudaStreamWaitEvent(rs, u.second, 0);
+      cudaEventDestroy(u.second);  // released once the wait is resolved
+    }
+    s->uses.clear();
+  }
+  void* arrays[] = {s->d_payload, s->d_chunk_word, s->d_brick_len, s->d_brick_off, s->d_desc, s->d_err};
+  for (void* a : arrays)
+    if (a) cudaFreeAsync(a, rs);  // rs null: the legacy stream, after the device synchronisation
+  if (rs) cudaStreamSynchronize(rs);
+  if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
   delete s;
 }
 
@@ -361,6 +410,7 @@ pc_status run_retrieve(const pc_streams* s, int k0, int k, const int64_t lo[3], 
     TimedLaunch tl(PC_KERNEL_RETRIEVE, st);
     CK(launch_retrieve(s->dtype, s->ndims, R, st));
   }
+  note_use(s, st);
   return PC_OK;
 }
 
@@ -385,6 +435,25 @@ void pcz::field_geometry(int ndims, const int64_t* dims, int64_t d3[3], int64_t 
   make_geometry(ndims, dims, d3, nb, nbricks, nchunks);
 }
 bool pcz::device_pointer(const void* p) { return is_device_ptr(p); }
+void pcz::note_use(const pc_streams* s, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(s->use_mu);
+  for (auto& u : s->uses)
+    if (u.first == st) {  // the new record follows every earlier launch on st
+      if (cudaEventRecord(u.second, st) != cudaSuccess) {
+        cudaGetLastError();
+        s->sync_device = true;
+      }
+      return;
+    }
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ev, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (ev) cudaEventDestroy(ev);
+    s->sync_device = true;
+    return;
+  }
+  s->uses.emplace_back(st, ev);
+}
 
 extern "C" {
 
@@ -490,7 +559,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
     if (e == cudaSuccess) e = streams_alloc((void**)&s->d_err, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
     if (e != cudaSuccess) {
-      streams_release(s);
+      streams_release(s, true);
       return cuda_fail(e, "allocation");
     }
     P.brick_off = s->d_brick_off;
@@ -576,7 +645,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
     if (rc == PC_OK) rc = upload_desc(s, st);  // synchronises: scratch is idle when freed
   }
   if (rc != PC_OK) {
-    streams_release(s);
+    streams_release(s, true);
     return rc;
   }
   *out = s;
@@ -616,19 +685,7 @@ pc_status pc_query_k(const pc_streams* s, double tau, int* k_out) {
 
 // A per-device stream of the library for copies between the device and
 // pinned host memory, so that they overlap the kernels of the caller's stream.
-static cudaStream_t copy_stream() {
-  static std::mutex mu;
-  static cudaStream_t streams[128] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(mu);
-  cudaStream_t& cs = streams[dev & 127];
-  if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    cs = nullptr;
-  }
-  return cs;
-}
+static cudaStream_t copy_stream() { return lib_stream(0); }
 
 // Retrieval into pinned host memory by slabs of whole brick layers along z:
 // each slab is decoded into one of two device staging buffers on the caller's
@@ -940,7 +997,7 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   }
   if (e == cudaSuccess) e = launch_brick_offsets(s->d_brick_len, s->d_brick_off, n, nbr, st);
   if (e != cudaSuccess) {
-    streams_release(s);
+    streams_release(s, true);
     return cuda_fail(e, "deserialize upload");
   }
   pc_status r = upload_desc(s, st);
@@ -955,7 +1012,7 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   }
   if (r == PC_OK && h_err) r = fail(PC_ERR_CORRUPT_STREAM, "a block does not parse");
   if (r != PC_OK) {
-    streams_release(s);
+    streams_release(s, true);
     return r;
   }
   *out = s;

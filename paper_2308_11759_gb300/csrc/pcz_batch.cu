@@ -994,6 +994,8 @@ pc_status pc_retrieve_batch(int nq, const pc_streams* const* s, const int* k, co
       cudaFreeAsync(mem, st);
       if (e != cudaSuccess) return api_cuda_fail(e, "batched retrieval");
     }
+  for (int q = 0; q < nq; ++q)
+    if (k[q] > 0) note_use(s[q], st);
   return PC_OK;
 }
 

@@ -5,7 +5,10 @@
 
 #include <cstdint>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -36,6 +39,13 @@ struct pc_streams {
   pcz::CompDesc* d_desc = nullptr;   // [n]
   unsigned int* d_err = nullptr;
   std::shared_ptr<void> backing;     // set when the device arrays live in arenas shared by a batch
+  // The library's launches that read the arrays: per stream an event recorded
+  // behind the latest one.  pc_streams_free waits for these, not for the
+  // whole device.  sync_device: an event could not be made, so it waits for
+  // the device instead.
+  mutable std::mutex use_mu;
+  mutable std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
+  mutable bool sync_device = false;
 };
 
 namespace pcz {
@@ -72,5 +82,7 @@ bool device_pointer(const void* p);
 // Stream-ordered scratch from the library's own memory pool (freed with
 // cudaFreeAsync on a stream).
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+// Records that work just queued on st reads the arrays of s.
+void note_use(const pc_streams* s, cudaStream_t st);
 
 }  // namespace pcz

@@ -245,3 +245,84 @@ def test_release_cached_memory(P):
     assert torch.equal(again.retrieve(k=3).cpu(), ref)
     again.close()
     live.close()
+
+
+def test_free_waits_for_its_own_work_only(P):
+    """pc_streams_free waits for the library's launches that read the streams,
+    on whatever stream they were queued, and not for unrelated work: (1) a
+    retrieval queued behind a backlog on one stream, then the streams freed
+    at once and their memory reused by another field's streams, still reads
+    intact streams; (2) freeing streams returns while another stream's
+    backlog is still running."""
+    x = S.powerlaw((192, 192, 192), seed=46, dtype=np.float32)
+    xd = torch.from_numpy(x).cuda()
+    tau = O.tau_decade(O.value_range(x), 8)
+    ref = P.compress(xd, tau)
+    want = ref.retrieve(k=8)
+    torch.cuda.synchronize()
+    a = torch.randn(8192, 8192, device="cuda")
+    sB, sC, sD = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    st = P.compress(xd, tau)
+    out = torch.empty_like(xd)
+    with torch.cuda.stream(sB):
+        b = a
+        for _ in range(8):
+            b = b @ a
+        st.retrieve(k=8, out=out, stream=sB)
+    st.close()  # returns once the retrieval on sB has run
+    y = torch.from_numpy(S.gaussians((192, 192, 192), seed=47, dtype=np.float32)).cuda()
+    torch.cuda.synchronize()
+    other = P.compress(y, tau, stream=sD)  # takes the freed pool blocks
+    sD.synchronize()
+    assert torch.equal(out.view(torch.int32), want.view(torch.int32))
+    with torch.cuda.stream(sC):
+        c = a
+        for _ in range(20):
+            c = c @ a
+    other.close()
+    assert not sC.query()  # the backlog on sC did not hold the free up
+    torch.cuda.synchronize()
+    ref.close()
+
+
+def test_calls_from_fresh_threads_on_their_own_streams(P):
+    """Each host thread (whose first CUDA call is the library's) runs one
+    field's pipeline -- range and schedule, compress and retrievals -- on its
+    own stream, from pinned host memory into pinned host memory; the results
+    equal the same calls made one after the other on the default stream."""
+    import threading
+
+    # the first output (42 MB) goes through the staging slabs, the second (7 MB) is written in place
+    xs = [S.powerlaw((256, 256, 160), seed=48, dtype=np.float32), S.fronts((96, 100, 90), seed=49)]
+    hin = [torch.from_numpy(x).pin_memory() for x in xs]
+    want = []
+    for h in hin:
+        st = P.compress(h, P.field_tau_schedule(h, "decade", 6))
+        want.append([st.retrieve(k=k).cpu() for k in (2, 6)])
+        st.close()
+    got = [None, None]
+    errors = []
+
+    def run(j):
+        try:
+            s = torch.cuda.Stream()
+            tau = P.field_tau_schedule(hin[j], "decade", 6, stream=s)
+            st = P.compress(hin[j], tau, stream=s)
+            outs = [torch.empty(hin[j].shape, dtype=hin[j].dtype).pin_memory() for _ in range(2)]
+            for o, k in zip(outs, (2, 6)):
+                st.retrieve(k=k, out=o, stream=s)
+            s.synchronize()
+            st.close()
+            got[j] = outs
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(j,)) for j in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for j in range(2):
+        for o, w in zip(got[j], want[j]):
+            assert torch.equal(o.view(torch.uint8), w.view(torch.uint8))
