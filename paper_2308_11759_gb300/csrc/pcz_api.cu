@@ -303,7 +303,7 @@ void streams_release(pc_streams* s, bool sync_device = false) {
     }
     s->uses.clear();
   }
-  void* arrays[] = {s->d_payload, s->d_chunk_word, s->d_brick_len, s->d_brick_off, s->d_desc, s->d_err};
+  void* arrays[] = {s->d_payload, s->d_index};
   for (void* a : arrays)
     if (a) cudaFreeAsync(a, rs);  // rs null: the legacy stream, after the device synchronisation
   if (rs) cudaStreamSynchronize(rs);
@@ -311,13 +311,60 @@ void streams_release(pc_streams* s, bool sync_device = false) {
   delete s;
 }
 
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// A small pinned host buffer per host thread for the results a call reads
+// back and the parameters it uploads (grown on demand; one copy each way).
+struct PinnedStage {
+  void* p = nullptr;
+  size_t cap = 0;
+  ~PinnedStage() {
+    if (p) cudaFreeHost(p);
+  }
+  void* get(size_t bytes) {
+    if (bytes > cap) {
+      if (p) cudaFreeHost(p);
+      p = nullptr;
+      cap = 0;
+      const size_t want = std::max(bytes, size_t(16) << 10);
+      if (cudaMallocHost(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return nullptr;
+      }
+      cap = want;
+    }
+    return p;
+  }
+};
+thread_local PinnedStage t_stage;
+
 // One device array of a pc_streams, from the library's pool on stream st.
 cudaError_t streams_alloc(void** p, size_t bytes, cudaStream_t st) { return pool_alloc(0, p, bytes, st); }
 cudaError_t payload_alloc(void** p, size_t bytes, cudaStream_t st) { return pool_alloc(1, p, bytes, st); }
 
-// Uploads the per-component descriptors the retrieval kernel reads.
-pc_status upload_desc(pc_streams* s, cudaStream_t st) {
-  std::vector<CompDesc> d(s->n);
+// The index arrays of s in one allocation (from the index pool): chunk word
+// offsets [n][nchunks] (u64), brick lengths [n][nbricks] (u16), brick bit
+// offsets [n][nbricks] (u32), the component descriptors and the error word,
+// which is cleared on st.
+cudaError_t alloc_index(pc_streams* s, cudaStream_t st) {
+  const size_t n = (size_t)s->n, nbr = (size_t)s->nbricks, nch = (size_t)s->nchunks;
+  const size_t o_cw = 0, o_bl = align256(o_cw + 8 * n * nch + 16), o_bo = align256(o_bl + 2 * n * nbr + 16);
+  const size_t o_desc = align256(o_bo + 4 * n * nbr + 16), o_err = align256(o_desc + sizeof(CompDesc) * n);
+  char* p = nullptr;
+  cudaError_t e = streams_alloc((void**)&p, o_err + 16, st);
+  if (e != cudaSuccess) return e;
+  s->d_index = p;
+  s->d_chunk_word = (uint64_t*)(p + o_cw);
+  s->d_brick_len = (uint16_t*)(p + o_bl);
+  s->d_brick_off = (uint32_t*)(p + o_bo);
+  s->d_desc = (CompDesc*)(p + o_desc);
+  s->d_err = (unsigned int*)(p + o_err);
+  return cudaMemsetAsync(s->d_err, 0, 16, st);
+}
+
+// The per-component descriptors the retrieval kernel reads.
+void fill_desc(const pc_streams* s, CompDesc* d) {
   for (int i = 0; i < s->n; ++i) {
     d[i].payload = s->d_payload + s->word_base[i];
     d[i].nwords = s->words[i];
@@ -327,6 +374,12 @@ pc_status upload_desc(pc_streams* s, cudaStream_t st) {
     d[i].L = s->L[i];
     d[i].pad_ = 0;
   }
+}
+
+// Uploads the descriptors and waits for them.
+pc_status upload_desc(pc_streams* s, cudaStream_t st) {
+  std::vector<CompDesc> d(s->n);
+  fill_desc(s, d.data());
   CK(cudaMemcpyAsync(s->d_desc, d.data(), sizeof(CompDesc) * s->n, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   return PC_OK;
@@ -520,48 +573,39 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
   {
     Scratch scr(st);
     cudaError_t e = cudaSuccess;
-#define SCR(ptr, bytes)                                             \
-  if (e == cudaSuccess) e = scr.get((void**)&(ptr), (size_t)(bytes));
     const void* d_field = field;
     void* staged = nullptr;
     bool mapped_host = false;
     if (!kernel_pointer(field, &d_field, &mapped_host)) {  // pageable host field: copy it in on the stream
-      SCR(staged, count * dsize(dtype));
+      e = scr.get(&staged, count * dsize(dtype));
       if (e == cudaSuccess) e = cudaMemcpyAsync(staged, field, count * dsize(dtype), cudaMemcpyHostToDevice, st);
       d_field = staged;
     }
     P.field = d_field;
-    uint32_t* chunk_nwords = nullptr;
-    uint64_t* chunk_pool = nullptr;
-    uint32_t* chunk_counts = nullptr;
-    uint64_t* totals = nullptr;
-    unsigned long long* counts = nullptr;
-    unsigned int* flags = nullptr;
-    unsigned long long* used = nullptr;
-    uint64_t* comp_base = nullptr;
-    uint64_t* chunk_maxerr = nullptr;
-    unsigned long long* maxerr = nullptr;
-    SCR(chunk_nwords, 4 * n * nch);
-    SCR(chunk_maxerr, 8 * n * nch);
-    SCR(maxerr, 8 * n);
-    SCR(chunk_pool, 8 * n * nch);
-    SCR(chunk_counts, 20 * n * nch);
-    SCR(totals, 8 * n);
-    SCR(counts, 8 * 5 * n);
-    SCR(flags, 16);
-    SCR(used, 16);
-    SCR(comp_base, 8 * n);
-#undef SCR
-    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16, st);
-    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16, st);
-    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16, st);
-    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_desc, sizeof(CompDesc) * n, st);
-    if (e == cudaSuccess) e = streams_alloc((void**)&s->d_err, 16, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
+    // one scratch block: the per-(component, chunk) arrays, then the call's
+    // results back to back (read with one copy), then the payload bases
+    const size_t nc = (size_t)n * nch;
+    const size_t o_nwords = 0, o_maxerr_c = align256(o_nwords + 4 * nc), o_pool = align256(o_maxerr_c + 8 * nc);
+    const size_t o_counts_c = align256(o_pool + 8 * nc), o_res = align256(o_counts_c + 20 * nc);
+    const size_t res_bytes = 56 * (size_t)n + 16;  // totals[n], counts[5n], maxerr[n], flags (8 bytes), used
+    const size_t o_base = align256(o_res + res_bytes), scratch_bytes = o_base + 8 * (size_t)n;
+    char* sb = nullptr;
+    if (e == cudaSuccess) e = scr.get((void**)&sb, scratch_bytes);
+    if (e == cudaSuccess) e = alloc_index(s, st);
     if (e != cudaSuccess) {
       streams_release(s, true);
       return cuda_fail(e, "allocation");
     }
+    uint32_t* chunk_nwords = (uint32_t*)(sb + o_nwords);
+    uint64_t* chunk_maxerr = (uint64_t*)(sb + o_maxerr_c);
+    uint64_t* chunk_pool = (uint64_t*)(sb + o_pool);
+    uint32_t* chunk_counts = (uint32_t*)(sb + o_counts_c);
+    uint64_t* totals = (uint64_t*)(sb + o_res);
+    unsigned long long* counts = (unsigned long long*)(totals + n);
+    unsigned long long* maxerr = counts + 5 * n;
+    unsigned int* flags = (unsigned int*)(maxerr + n);
+    unsigned long long* used = (unsigned long long*)(maxerr + n) + 1;
+    uint64_t* comp_base = (uint64_t*)(sb + o_base);
     P.brick_off = s->d_brick_off;
     P.chunk_nwords = chunk_nwords;
     P.chunk_pool = chunk_pool;
@@ -571,12 +615,20 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
     P.flags = flags;
     P.pool_used = used;
 
-    std::vector<uint64_t> h_tot(n);
-    std::vector<unsigned long long> h_cnt(5 * n), h_merr(n);
+    // the results come back through this thread's pinned staging buffer
+    const size_t up_bytes = 8 * (size_t)n + sizeof(CompDesc) * (size_t)n;  // payload bases, descriptors
+    char* h = static_cast<char*>(t_stage.get(std::max(res_bytes, up_bytes)));
+    if (!h) {
+      streams_release(s, true);
+      return fail(PC_ERR_OOM, "pinned staging buffer");
+    }
+    const uint64_t* h_tot = (const uint64_t*)h;
+    const unsigned long long* h_cnt = (const unsigned long long*)(h_tot + n);
+    const unsigned long long* h_merr = h_cnt + 5 * n;
     unsigned int h_flags = 0;
     unsigned long long h_used = 0;
     // the pool is shared by every call on this device: hold it until the
-    // packing kernel that reads it has finished (upload_desc synchronises)
+    // packing kernel that reads it has finished (the last synchronisation)
     std::unique_lock<std::mutex> pool_lock(g_mu);
     for (int attempt = 0; attempt < 3; ++attempt) {
       {
@@ -595,8 +647,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
         P.pool = cx.pool;
         P.pool_words = cx.pool_words;
       }
-      if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 16, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, 16, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 16, st);  // flags and the pool's bump counter
       if (e == cudaSuccess) {
         TimedLaunch tl(PC_KERNEL_COMPRESS, st);
         e = launch_compress(dtype, ndims, P, st, !mapped_host);
@@ -606,13 +657,11 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
         e = launch_scan_chunks(chunk_nwords, s->d_chunk_word, totals, chunk_counts, counts, chunk_maxerr, maxerr, n,
                                nch, st);
       }
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h_tot.data(), totals, 8 * n, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt.data(), counts, 8 * 5 * n, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h_merr.data(), maxerr, 8 * n, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, flags, 4, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&h_used, used, 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h, totals, res_bytes, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) break;
+      h_flags = *(const unsigned int*)(h_merr + n);
+      h_used = *((const unsigned long long*)(h_merr + n) + 1);
       if (!(h_flags & kFlagPoolOverflow)) break;
     }
     if (e != cudaSuccess) {
@@ -625,9 +674,7 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
       rc = fail(PC_ERR_OOM, "scratch pool could not be sized");
     } else {
       uint64_t total = 0;
-      std::vector<uint64_t> base(n);
       for (int i = 0; i < n; ++i) {
-        base[i] = total;
         s->word_base[i] = total;
         s->words[i] = h_tot[i];
         total += h_tot[i];
@@ -635,14 +682,24 @@ pc_status pc_compress(const void* field, const int64_t* dims, int ndims, pc_dtyp
         s->measured[i] = bits_to_double(h_merr[i], dtype);
       }
       e = payload_alloc((void**)&s->d_payload, 8 * total + 16, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(comp_base, base.data(), 8 * n, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) {
+        // payload bases and the retrieval's descriptors, staged together (the results are read)
+        uint64_t* h_base = (uint64_t*)h;
+        CompDesc* h_desc = (CompDesc*)(h + 8 * (size_t)n);
+        for (int i = 0; i < n; ++i) h_base[i] = s->word_base[i];
+        fill_desc(s, h_desc);
+        e = cudaMemcpyAsync(comp_base, h_base, 8 * (size_t)n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(s->d_desc, h_desc, sizeof(CompDesc) * (size_t)n, cudaMemcpyHostToDevice, st);
+      }
       if (e == cudaSuccess) {
         TimedLaunch tl(PC_KERNEL_PACK, st);
         e = launch_pack(P.pool, chunk_nwords, chunk_pool, s->d_chunk_word, comp_base, s->d_payload, n, nch, st);
       }
+      // the staging buffer, the bit pool and the scratch are idle once this returns
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) rc = cuda_fail(e, "pack");
     }
-    if (rc == PC_OK) rc = upload_desc(s, st);  // synchronises: scratch is idle when freed
   }
   if (rc != PC_OK) {
     streams_release(s, true);
@@ -979,12 +1036,7 @@ pc_status pc_streams_deserialize(const void* h_buf, size_t len, void* cuda_strea
   cudaError_t e = cudaGetDevice(&dev);
   s->device = dev;
   if (e == cudaSuccess) e = payload_alloc((void**)&s->d_payload, 8 * total + 16, st);
-  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_len, 2 * (size_t)n * nbr + 16, st);
-  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_chunk_word, 8 * (size_t)n * nch + 16, st);
-  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_brick_off, 4 * (size_t)n * nbr + 16, st);
-  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_desc, sizeof(CompDesc) * n, st);
-  if (e == cudaSuccess) e = streams_alloc((void**)&s->d_err, 16, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 16, st);
+  if (e == cudaSuccess) e = alloc_index(s, st);
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     e = cudaMemcpyAsync(s->d_chunk_word + (int64_t)i * nch, p + off, 8 * nch, cudaMemcpyHostToDevice, st);
     off += 8 * nch;

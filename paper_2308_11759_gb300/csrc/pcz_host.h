@@ -38,6 +38,7 @@ struct pc_streams {
   uint32_t* d_brick_off = nullptr;   // [n][nbricks] derived: first bit of each brick in its chunk
   pcz::CompDesc* d_desc = nullptr;   // [n]
   unsigned int* d_err = nullptr;
+  void* d_index = nullptr;           // the allocation holding chunk words .. d_err (none for a batch's streams)
   std::shared_ptr<void> backing;     // set when the device arrays live in arenas shared by a batch
   // The library's launches that read the arrays: per stream an event recorded
   // behind the latest one.  pc_streams_free waits for these, not for the
