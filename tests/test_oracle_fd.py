@@ -41,10 +41,24 @@ def test_vorticity_of_rigid_rotation_and_shear():
     assert np.array_equal(D.vorticity_z(-y, x), np.full(x.shape, 2.0))
     # u = y^2, v = x^2: omega_z = 2x - 2y (exact on quadratics, ends included)
     assert np.array_equal(D.vorticity_z(y * y, x * x), 2.0 * x - 2.0 * y)
-    # float32 fields: the float64 result rounded once
+    # float32 fields are differentiated in float32 (exact here: small integers)
     u32, v32 = (y * y).astype(np.float32), (x * x).astype(np.float32)
     w = D.vorticity_z(u32, v32)
     assert w.dtype == np.float32 and np.array_equal(w, (2.0 * x - 2.0 * y).astype(np.float32))
+
+
+def test_float32_fields_are_differentiated_in_float32():
+    # one float32 rounding per operation: on random data some results differ
+    # from the float64 computation rounded once, and all lie within a few
+    # float32 ulps of it
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((6, 7, 1000)).astype(np.float32)
+    for axis, fn in ((0, D.first_derivative), (2, D.second_derivative)):
+        d32 = fn(f, axis, 0.1)
+        d64 = fn(f.astype(np.float64), axis, 0.1)
+        assert d32.dtype == np.float32
+        assert (d32 != d64.astype(np.float32)).any()
+        assert np.allclose(d32, d64, rtol=1e-4, atol=1e-4 * np.abs(d64).max())
 
 
 def test_first_derivative_matches_numpy_gradient():
