@@ -244,6 +244,29 @@ pc_status pc_lossless_sweep(const void *field, const int64_t *dims, int ndims, p
                             void *cuda_stream, pc_streams **out, int *k, double *bits_per_value);
 
 /*
+ * Derivatives of (reconstructed) fields on a regular grid of spacing h: the
+ * operators of the progressive use case (Sec. 5.3), where the vorticity
+ * component v_x - u_y and the second derivative w_zz of a velocity field
+ * magnify the reconstruction error like h^-1 and h^-2.  Second-order
+ * differences at every point: central inside; at the two ends of the axis
+ * ((4 f1 - 3 f0) - f2) / (2h) and ((3 f[n-1] - 4 f[n-2]) + f[n-3]) / (2h) for a
+ * first derivative, (((2 f0 - 5 f1) + 4 f2) - f3) / h^2 and its mirror image
+ * for a second.  Arithmetic in dtype, one rounding per operation in that
+ * order, with h rounded to dtype first.
+ *   pc_fd_vorticity_z: out = v_x - u_y.  u, v, out: device pointers to
+ *     prod(dims) values of dtype, dims[0] = nx fastest; ndims 2 or 3; nx >= 3
+ *     and ny >= 3.
+ *   pc_fd_second: out = d2w/da2 along axis a (0 = x, 1 = y, 2 = z; a < ndims,
+ *     ndims 1..3), at least 4 points along it.
+ * out must not overlap an input.  h > 0 and finite.  PC_ERR_ARG otherwise.
+ * Asynchronous on cuda_stream.
+ */
+pc_status pc_fd_vorticity_z(const void *u, const void *v, const int64_t *dims, int ndims, pc_dtype dtype, double h,
+                            void *out, void *cuda_stream);
+pc_status pc_fd_second(const void *w, const int64_t *dims, int ndims, pc_dtype dtype, int axis, double h, void *out,
+                       void *cuda_stream);
+
+/*
  * Kernel timing (instrumentation, off by default).  While enabled, every
  * kernel the library launches is bracketed by CUDA events recorded on the
  * stream it is launched on.  pc_timing_read synchronises the device and
@@ -257,7 +280,8 @@ typedef enum {
   PC_KERNEL_PACK = 2,     /* chunk copy into the streams */
   PC_KERNEL_RETRIEVE = 3, /* fused reconstruction, Algorithm 2 */
   PC_KERNEL_RANGE = 4,    /* field min/max */
-  PC_KERNEL_KINDS = 5
+  PC_KERNEL_FD = 5,       /* finite-difference derivatives */
+  PC_KERNEL_KINDS = 6
 } pc_kernel_kind;
 pc_status pc_timing_enable(int on);
 pc_status pc_timing_read(double *ms, uint64_t *launches);

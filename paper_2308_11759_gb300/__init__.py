@@ -104,6 +104,8 @@ def lib():
             "pc_tau_schedule": [C.c_int, C.c_double, C.c_int, C.c_int, dp],
             "pc_field_tau_schedule": [vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, vp, dp],
             "pc_lossless_sweep": [vp, i64p, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.POINTER(vp), ip, dp],
+            "pc_fd_vorticity_z": [vp, vp, i64p, C.c_int, C.c_int, C.c_double, vp, vp],
+            "pc_fd_second": [vp, i64p, C.c_int, C.c_int, C.c_int, C.c_double, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -514,6 +516,40 @@ def field_range(x, stream=None):
     return lo.value, hi.value
 
 
+# ---- derivatives of reconstructions (Sec. 5.3, the progressive use case) ----
+
+
+def _fd_out(x, out):
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(x)
+    if out.shape != x.shape or out.dtype != x.dtype:
+        raise ValueError("out must have the input's shape and type")
+    return out
+
+
+def fd_vorticity_z(u, v, h: float = 1.0, out=None, stream=None):
+    """omega_z = v_x - u_y of device tensors u, v of shape (nz, ny, nx) or
+    (ny, nx), grid spacing h (pc_fd_vorticity_z)."""
+    if u.shape != v.shape or u.dtype != v.dtype:
+        raise ValueError("u and v must have one shape and one type")
+    out = _fd_out(u, out)
+    dims = (C.c_int64 * u.dim())(*reversed(u.shape))
+    _check(lib().pc_fd_vorticity_z(_ptr(u), _ptr(v), dims, u.dim(), _dtype_code(u.dtype), float(h), _ptr(out),
+                                   _stream_ptr(stream)))
+    return out
+
+
+def fd_second(w, axis: int, h: float = 1.0, out=None, stream=None):
+    """The second derivative of device tensor w along grid axis `axis` (0 = x,
+    the last tensor dimension), grid spacing h (pc_fd_second)."""
+    out = _fd_out(w, out)
+    dims = (C.c_int64 * w.dim())(*reversed(w.shape))
+    _check(lib().pc_fd_second(_ptr(w), dims, w.dim(), _dtype_code(w.dtype), int(axis), float(h), _ptr(out),
+                              _stream_ptr(stream)))
+    return out
+
+
 # ---- tolerance schedules (Sec. 5.1: tau_i = 2^(-delta i) tau_0, tau_0 = range) ----
 
 PC_TAU_BINARY, PC_TAU_DECADE = 1, 2
@@ -578,7 +614,7 @@ def debug_status(reset: bool = False):
     return int(w.value), bool(en.value)
 
 
-KERNEL_KINDS = ("compress", "scan", "pack", "retrieve", "range")
+KERNEL_KINDS = ("compress", "scan", "pack", "retrieve", "range", "fd")
 
 
 def release_cached_memory():
@@ -594,7 +630,7 @@ def timing_enable(on: bool = True):
 
 def timing_read():
     """{kernel kind: (total ms, launches)} since timing_enable."""
-    ms = (C.c_double * 5)()
-    n = (C.c_uint64 * 5)()
+    ms = (C.c_double * len(KERNEL_KINDS))()
+    n = (C.c_uint64 * len(KERNEL_KINDS))()
     _check(lib().pc_timing_read(ms, n))
     return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_KINDS)}

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpcz.so")
 LIB_DEBUG = os.path.join(HERE, "libpcz_debug.so")  # with the PCZ_DEBUG buffer checks
-SOURCES = ["pcz_api.cu", "pcz_compress.cu", "pcz_retrieve.cu", "pcz_misc.cu", "pcz_noalloc.cu", "pcz_small.cu", "pcz_serve.cu", "pcz_batch.cu", "pcz_schedule.cu"]
+SOURCES = ["pcz_api.cu", "pcz_compress.cu", "pcz_retrieve.cu", "pcz_misc.cu", "pcz_noalloc.cu", "pcz_small.cu", "pcz_serve.cu", "pcz_batch.cu", "pcz_schedule.cu", "pcz_fd.cu"]
 HEADERS = ["pcz_device.cuh", "pcz_kernels.h", "pcz_host.h", "pcz_chunk3.cuh", "pcz_chunk_small.cuh", os.path.join("..", "..", "include", "pcz.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1100,6 +1100,62 @@ pc_status pc_stream_read(const pc_streams* s, int i, uint64_t word_off, uint64_t
 
 void pc_streams_free(pc_streams* s) { streams_release(s); }
 
+// The extents and checks shared by the derivative calls: nx, ny, nz of a
+// field of 1..3 dimensions (PC_ERR_ARG on a bad argument).
+static pc_status fd_check(const int64_t* dims, int ndims, pc_dtype dtype, double h, int64_t d3[3]) {
+  if (!dims || ndims < 1 || ndims > 3) return fail(PC_ERR_ARG, "ndims must be 1, 2 or 3");
+  if (dtype != PC_F32 && dtype != PC_F64) return fail(PC_ERR_ARG, "bad dtype");
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(PC_ERR_ARG, "h must be positive and finite");
+  for (int a = 0; a < 3; ++a) {
+    d3[a] = a < ndims ? dims[a] : 1;
+    if (d3[a] < 1) return fail(PC_ERR_ARG, "extent < 1");
+  }
+  if (d3[0] > (int64_t(1) << 40) / d3[1] / d3[2]) return fail(PC_ERR_ARG, "field too large");
+  return PC_OK;
+}
+
+// True when [a, a + n) and [b, b + n) share a byte.
+static bool overlaps(const void* a, const void* b, size_t n) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + n && y < x + n;
+}
+
+pc_status pc_fd_vorticity_z(const void* u, const void* v, const int64_t* dims, int ndims, pc_dtype dtype, double h,
+                            void* out, void* cuda_stream) {
+  TraceRange trace_("pc_fd_vorticity_z");
+  g_err.clear();
+  int64_t d3[3];
+  pc_status r = fd_check(dims, ndims, dtype, h, d3);
+  if (r != PC_OK) return r;
+  if (ndims < 2 || d3[0] < 3 || d3[1] < 3) return fail(PC_ERR_ARG, "v_x - u_y needs ndims >= 2, nx >= 3 and ny >= 3");
+  if (!u || !v || !out || !is_device_ptr(u) || !is_device_ptr(v) || !is_device_ptr(out))
+    return fail(PC_ERR_ARG, "u, v and out must be device memory");
+  const size_t bytes = (size_t)(d3[0] * d3[1] * d3[2]) * dsize(dtype);
+  if (overlaps(out, u, bytes) || overlaps(out, v, bytes)) return fail(PC_ERR_ARG, "out overlaps an input");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TimedLaunch tl(PC_KERNEL_FD, st);
+  CK(launch_fd_vorticity_z(dtype, u, v, out, d3[0], d3[1], d3[2], h, st));
+  return PC_OK;
+}
+
+pc_status pc_fd_second(const void* w, const int64_t* dims, int ndims, pc_dtype dtype, int axis, double h, void* out,
+                       void* cuda_stream) {
+  TraceRange trace_("pc_fd_second");
+  g_err.clear();
+  int64_t d3[3];
+  pc_status r = fd_check(dims, ndims, dtype, h, d3);
+  if (r != PC_OK) return r;
+  if (axis < 0 || axis >= ndims) return fail(PC_ERR_ARG, "axis must be below ndims");
+  if (d3[axis] < 4) return fail(PC_ERR_ARG, "a second derivative needs 4 points along the axis");
+  if (!w || !out || !is_device_ptr(w) || !is_device_ptr(out)) return fail(PC_ERR_ARG, "w and out must be device memory");
+  const size_t bytes = (size_t)(d3[0] * d3[1] * d3[2]) * dsize(dtype);
+  if (overlaps(out, w, bytes)) return fail(PC_ERR_ARG, "out overlaps the input");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TimedLaunch tl(PC_KERNEL_FD, st);
+  CK(launch_fd_second(dtype, w, out, d3[0], d3[1], d3[2], axis, h, st));
+  return PC_OK;
+}
+
 pc_status pc_release_cached_memory(void) {
   g_err.clear();
   int cur = 0;

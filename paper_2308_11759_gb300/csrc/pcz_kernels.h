@@ -175,4 +175,11 @@ int retrieve_grid(int dtype, int ndims, int64_t nunits);
 int retrieve_unit_mult(int ncomp);
 size_t retrieve_spill_words(int dtype, int ndims, int grid);
 
+// Finite-difference derivatives (pcz_fd.cu): omega_z = v_x - u_y and the
+// second derivative along one axis, over nx * ny * nz values.
+cudaError_t launch_fd_vorticity_z(int dtype, const void* u, const void* v, void* out, int64_t nx, int64_t ny,
+                                  int64_t nz, double h, cudaStream_t st);
+cudaError_t launch_fd_second(int dtype, const void* w, void* out, int64_t nx, int64_t ny, int64_t nz, int axis,
+                             double h, cudaStream_t st);
+
 }  // namespace pcz
