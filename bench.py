@@ -766,6 +766,68 @@ def run_config1(args, device, nthreads):
             "oracle_single_core": oc[1], "oracle_all_cores": oc[nthreads]}
 
 
+def run_use_case(args, device):
+    """Sec. 5.3's progressive use case on a synthetic stand-in for a velocity
+    field (three k^-5/3 components, 384 x 384 x 256 float64, the shape of the
+    paper's Miranda field, scaled to standard deviation 4), each compressed
+    with the tolerances of the paper's figure, tau = 1, 2^-4, 2^-9: per k the
+    errors of the velocity, of omega_z = v_x - u_y and of w_zz against the
+    derivatives of the original field; then the derivative kernels timed
+    against the HBM roofline on float64 and float32 fields."""
+    import torch
+
+    import paper_2308_11759_gb300 as pcz
+    import synth_fields as S
+
+    shape = (256, 384, 384)  # (nz, ny, nx)
+    tau = [1.0, 2.0 ** -4, 2.0 ** -9]
+    vel = [S.powerlaw(shape, seed=700 + c, dtype=np.float64, device=device) * 4.0 for c in range(3)]
+    streams = [pcz.compress(c, tau) for c in vel]
+    om_ref = pcz.fd_vorticity_z(vel[0], vel[1])
+    wzz_ref = pcz.fd_second(vel[2], 2)
+    om_max, wzz_max = float(om_ref.abs().max()), float(wzz_ref.abs().max())
+    per_k = []
+    for k in range(1, 4):
+        rec = [st.retrieve(k=k) for st in streams]
+        d_vel = max(float((r - c).abs().max()) for r, c in zip(rec, vel))
+        d_om = float((pcz.fd_vorticity_z(rec[0], rec[1]) - om_ref).abs().max())
+        d_wzz = float((pcz.fd_second(rec[2], 2) - wzz_ref).abs().max())
+        bits = sum(sum(st.info(i)[1] + 8 * st.info(i)[2] for i in range(k)) for st in streams) / (3 * rec[0].numel())
+        per_k.append({"k": k, "tau": tau[k - 1], "bits_per_value": round(bits, 3),
+                      "velocity_max_err": float("%.4g" % d_vel),
+                      "vorticity_max_err": float("%.4g" % d_om), "vorticity_rel": float("%.4g" % (d_om / om_max)),
+                      "w_zz_max_err": float("%.4g" % d_wzz), "w_zz_rel": float("%.4g" % (d_wzz / wzz_max))})
+        del rec
+    for st in streams:
+        st.close()
+    # the kernels: fields larger than L2, so every timed launch reads DRAM
+    hbm, _ = peaks()
+    kern = {}
+    reps = max(5, args.steps)
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        u, v, w = (c.to(dt) for c in vel)
+        out = torch.empty_like(u)
+        nb = u.numel() * u.element_size()
+        res = {}
+        for op, fn, nbytes in (("vorticity_z", lambda: pcz.fd_vorticity_z(u, v, out=out), 3 * nb),
+                               ("w_zz", lambda: pcz.fd_second(w, 2, out=out), 2 * nb)):
+            fn()
+            pcz.timing_enable(True)
+            for _ in range(reps):
+                fn()
+            kt = pcz.timing_read()
+            pcz.timing_enable(False)
+            ms = kt["fd"][0] / max(kt["fd"][1], 1)
+            res[op] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                       "roofline_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4),
+                       "algorithmic_bytes": nbytes}
+        kern[name] = res
+        del u, v, w, out
+    return {"workload": "3 float64 components of 384 x 384 x 256 (k^-5/3, std 4), tau = 1, 2^-4, 2^-9, h = 1",
+            "per_k": per_k, "vorticity_max": round(om_max, 4), "w_zz_max": round(wzz_max, 4),
+            "kernels": kern, "bound": "hbm (algorithmic bytes: inputs read once, output written once)"}
+
+
 def run_config5(args, device, nthreads):
     """The near-lossless large configuration: a 1024^3 float64 k^-5/3 field plus
     sharp tanh fronts (8 GiB), 12 components, tau_i = 10^-i * range: compress,
@@ -940,6 +1002,7 @@ def main():
     ap.add_argument("--serve-queries", type=int, default=10000)
     ap.add_argument("--serve-size", type=int, default=256)
     ap.add_argument("--no-configs", action="store_true", help="skip the 64^3 and 1024^3 configuration legs")
+    ap.add_argument("--no-use-case", action="store_true", help="skip the derivatives-of-reconstructions leg")
     ap.add_argument("--c5-size", type=int, default=1024)
     ap.add_argument("--c5-queries", type=int, default=2000)
     args = ap.parse_args()
@@ -990,6 +1053,7 @@ def main():
         configs = {"c1_64cube_f64": run_config1(args, device, nthreads),
                    "c5_1024cube_f64_fronts": run_config5(args, device, nthreads)}
     batched = None if args.no_batched else run_batched(args, device)
+    use_case = None if args.no_use_case else run_use_case(args, device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1036,6 +1100,7 @@ def main():
             "configurations": configs,
             "batched": batched,
             "serving": serving,
+            "use_case_derivatives": use_case,
         }
         print(json.dumps(line))
     if world > 1:

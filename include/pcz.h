@@ -258,7 +258,8 @@ pc_status pc_lossless_sweep(const void *field, const int64_t *dims, int ndims, p
  *     and ny >= 3.
  *   pc_fd_second: out = d2w/da2 along axis a (0 = x, 1 = y, 2 = z; a < ndims,
  *     ndims 1..3), at least 4 points along it.
- * out must not overlap an input.  h > 0 and finite.  PC_ERR_ARG otherwise.
+ * out must not overlap an input.  h > 0 and finite.  Extents below 2^31 (ny
+ * at most 524280).  PC_ERR_ARG otherwise.
  * Asynchronous on cuda_stream.
  */
 pc_status pc_fd_vorticity_z(const void *u, const void *v, const int64_t *dims, int ndims, pc_dtype dtype, double h,

@@ -1111,6 +1111,7 @@ static pc_status fd_check(const int64_t* dims, int ndims, pc_dtype dtype, double
     if (d3[a] < 1) return fail(PC_ERR_ARG, "extent < 1");
   }
   if (d3[0] > (int64_t(1) << 40) / d3[1] / d3[2]) return fail(PC_ERR_ARG, "field too large");
+  if (d3[0] > INT32_MAX || d3[1] > 8 * 65535 || d3[2] > INT32_MAX) return fail(PC_ERR_ARG, "an extent is too large");
   return PC_OK;
 }
 

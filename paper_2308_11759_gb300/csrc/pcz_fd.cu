@@ -14,10 +14,16 @@
 // division by a power of two is done as the exact multiplication by its
 // reciprocal (the same result); other spacings divide.
 //
-// Layout: x fastest, rows of nx values (row r = y + ny z).  The kernels are
-// bound by memory: a block takes segments of 256 consecutive values of a row
-// (coalesced loads and stores); the neighbouring rows and planes a stencil
-// reads come back from L1/L2, so each input is read from DRAM about once.
+// Layout: x fastest.  A CTA is a tile of 32 x 8 grid columns (x, y); each
+// thread walks its column through a slice of z, so no index is divided per
+// value and a second derivative along z keeps its three-point window in
+// registers (each value loaded once).  Neighbours along x and y come from
+// L1/L2.  Each input is read from DRAM about once and the output written
+// once: the kernels are bound by memory -- for float64 on GB300, whose FP64
+// rate is low, by the FP64 pipe, which is why powers of two scale the
+// exponent field with integer instructions where the result stays normal
+// (the same value as the multiplication).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -35,6 +41,8 @@ struct Ar<float> {
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  // x * 2^k, with p = 2^k
+  static __device__ __forceinline__ float mul2k(float x, int, float p) { return __fmul_rn(x, p); }
 };
 template <>
 struct Ar<double> {
@@ -42,68 +50,177 @@ struct Ar<double> {
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  // x * 2^k (p = 2^k): when x and the result are normal the product is x with
+  // k added to its exponent field, exactly the value the multiplication
+  // gives; zeros, subnormals, infinities, NaN and results leaving the normal
+  // range take the multiplication.
+  static __device__ __forceinline__ double mul2k(double x, int k, double p) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e != 0 && e != 0x7ff && e + k >= 1 && e + k <= 2046) return __longlong_as_double(b + ((long long)k << 52));
+    return __dmul_rn(x, p);
+  }
 };
 
-// Division by the denominator d (2h or h^2 in T): by the exact reciprocal
-// when d is a power of two, else a correctly rounded division.
+// Division by the denominator d (2h or h^2 in T): when d = 2^-k is a power of
+// two, the exact scaling by its reciprocal 2^k; else a correctly rounded
+// division.
 template <typename T>
 struct Den {
   T d, inv;
-  int pow2;
-  __device__ __forceinline__ T apply(T x) const { return pow2 ? Ar<T>::mul(x, inv) : Ar<T>::div(x, d); }
+  int pow2, k;
+  __device__ __forceinline__ T apply(T x) const { return pow2 ? Ar<T>::mul2k(x, k, inv) : Ar<T>::div(x, d); }
 };
 
 // First derivative at coordinate c of n along a line of stride s from p
 // (p points at the value at c).
 template <typename T>
-__device__ __forceinline__ T first_at(const T* __restrict__ p, int64_t c, int64_t n, int64_t s, const Den<T>& h2) {
+__device__ __forceinline__ T first_at(const T* __restrict__ p, int c, int n, int64_t s, const Den<T>& h2) {
   using A = Ar<T>;
   if (c > 0 && c < n - 1) return h2.apply(A::sub(__ldg(p + s), __ldg(p - s)));
   if (c == 0)
-    return h2.apply(A::sub(A::sub(A::mul(T(4), __ldg(p + s)), A::mul(T(3), __ldg(p))), __ldg(p + 2 * s)));
-  return h2.apply(A::add(A::sub(A::mul(T(3), __ldg(p)), A::mul(T(4), __ldg(p - s))), __ldg(p - 2 * s)));
+    return h2.apply(A::sub(A::sub(A::mul2k(__ldg(p + s), 2, T(4)), A::mul(T(3), __ldg(p))), __ldg(p + 2 * s)));
+  return h2.apply(A::add(A::sub(A::mul(T(3), __ldg(p)), A::mul2k(__ldg(p - s), 2, T(4))), __ldg(p - 2 * s)));
 }
 
 template <typename T>
-__device__ __forceinline__ T second_at(const T* __restrict__ p, int64_t c, int64_t n, int64_t s, const Den<T>& hh) {
+__device__ __forceinline__ T second_inner(T fp, T f0, T fm, const Den<T>& hh) {
   using A = Ar<T>;
-  if (c > 0 && c < n - 1) return hh.apply(A::add(A::sub(__ldg(p + s), A::mul(T(2), __ldg(p))), __ldg(p - s)));
+  return hh.apply(A::add(A::sub(fp, A::mul2k(f0, 1, T(2))), fm));
+}
+
+template <typename T>
+__device__ __forceinline__ T second_at(const T* __restrict__ p, int c, int n, int64_t s, const Den<T>& hh) {
+  using A = Ar<T>;
+  if (c > 0 && c < n - 1) return second_inner<T>(__ldg(p + s), __ldg(p), __ldg(p - s), hh);
   const int64_t d = c == 0 ? s : -s;  // towards the inside
-  return hh.apply(A::sub(A::add(A::sub(A::mul(T(2), __ldg(p)), A::mul(T(5), __ldg(p + d))), A::mul(T(4), __ldg(p + 2 * d))),
+  return hh.apply(A::sub(A::add(A::sub(A::mul2k(__ldg(p), 1, T(2)), A::mul(T(5), __ldg(p + d))),
+                                A::mul2k(__ldg(p + 2 * d), 2, T(4))),
                          __ldg(p + 3 * d)));
 }
 
-constexpr int kFdThreads = 256;
+constexpr int kTileX = 32, kTileY = 8;
 
-// omega_z = v_x - u_y over rows = ny * nz rows of nx values.
+// Thread (x, y) of a tile: its column and slice [z0, z1) of z.
+struct Column {
+  int x, y, z0, z1;
+  bool ok;
+};
+__device__ __forceinline__ Column column(int nx, int ny, int nz, int zchunk) {
+  Column c;
+  c.x = blockIdx.x * kTileX + threadIdx.x;
+  c.y = blockIdx.y * kTileY + threadIdx.y;
+  c.z0 = blockIdx.z * zchunk;
+  c.z1 = min(nz, c.z0 + zchunk);
+  c.ok = c.x < nx && c.y < ny;
+  return c;
+}
+
+// omega_z = v_x - u_y.
 template <typename T>
-__global__ void __launch_bounds__(kFdThreads) k_vorticity_z(const T* __restrict__ u, const T* __restrict__ v,
-                                                            T* __restrict__ out, int64_t nx, int64_t ny,
-                                                            int64_t rows, Den<T> h2) {
-  const int64_t segs = (nx + kFdThreads - 1) / kFdThreads;
-  for (int64_t g = blockIdx.x; g < rows * segs; g += gridDim.x) {
-    const int64_t r = g / segs, x = (g - r * segs) * kFdThreads + threadIdx.x;
-    if (x >= nx) continue;
-    const int64_t y = r % ny, i = r * nx + x;
-    const T vx = first_at<T>(v + i, x, nx, 1, h2);
-    const T uy = first_at<T>(u + i, y, ny, nx, h2);
-    out[i] = Ar<T>::sub(vx, uy);
+__global__ void __launch_bounds__(kTileX * kTileY) k_vorticity_z(const T* __restrict__ u, const T* __restrict__ v,
+                                                                 T* __restrict__ out, int nx, int ny, int nz,
+                                                                 int zchunk, Den<T> h2) {
+  const Column c = column(nx, ny, nz, zchunk);
+  if (!c.ok) return;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t i0 = ((int64_t)c.z0 * ny + c.y) * nx + c.x;
+  int z = c.z0;
+  if (c.x > 0 && c.x < nx - 1 && c.y > 0 && c.y < ny - 1) {
+    // interior column: the loads of 4 planes are issued before any is used
+    using A = Ar<T>;
+    for (; z + 4 <= c.z1; z += 4) {
+      const int64_t i = i0 + (int64_t)(z - c.z0) * plane;
+      T vp[4], vm[4], up[4], um[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        vp[j] = __ldg(v + i + j * plane + 1);
+        vm[j] = __ldg(v + i + j * plane - 1);
+        up[j] = __ldg(u + i + j * plane + nx);
+        um[j] = __ldg(u + i + j * plane - nx);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        out[i + j * plane] = A::sub(h2.apply(A::sub(vp[j], vm[j])), h2.apply(A::sub(up[j], um[j])));
+    }
+  }
+  for (; z < c.z1; ++z) {
+    const int64_t i = i0 + (int64_t)(z - c.z0) * plane;
+    out[i] = Ar<T>::sub(first_at<T>(v + i, c.x, nx, 1, h2), first_at<T>(u + i, c.y, ny, nx, h2));
   }
 }
 
-// d2w/da2 along the axis of coordinate extent n and stride s (a = 0, 1, 2:
-// x, y = r % ny, z = r / ny).
+// d2w/da2 along x (axis 0) or y (axis 1).
 template <typename T>
-__global__ void __launch_bounds__(kFdThreads) k_second(const T* __restrict__ w, T* __restrict__ out, int64_t nx,
-                                                       int64_t ny, int64_t rows, int axis, int64_t n, int64_t s,
-                                                       Den<T> hh) {
-  const int64_t segs = (nx + kFdThreads - 1) / kFdThreads;
-  for (int64_t g = blockIdx.x; g < rows * segs; g += gridDim.x) {
-    const int64_t r = g / segs, x = (g - r * segs) * kFdThreads + threadIdx.x;
-    if (x >= nx) continue;
-    const int64_t c = axis == 0 ? x : axis == 1 ? r % ny : r / ny;
-    const int64_t i = r * nx + x;
-    out[i] = second_at<T>(w + i, c, n, s, hh);
+__global__ void __launch_bounds__(kTileX * kTileY) k_second_xy(const T* __restrict__ w, T* __restrict__ out, int nx,
+                                                               int ny, int nz, int zchunk, int axis, Den<T> hh) {
+  const Column c = column(nx, ny, nz, zchunk);
+  if (!c.ok) return;
+  const int64_t plane = (int64_t)nx * ny;
+  const int cc = axis == 0 ? c.x : c.y, n = axis == 0 ? nx : ny;
+  const int64_t s = axis == 0 ? 1 : nx;
+  const int64_t i0 = ((int64_t)c.z0 * ny + c.y) * nx + c.x;
+  int z = c.z0;
+  if (cc > 0 && cc < n - 1) {  // interior column: 4 planes' loads in flight together
+    for (; z + 4 <= c.z1; z += 4) {
+      const int64_t i = i0 + (int64_t)(z - c.z0) * plane;
+      T fp[4], f0[4], fm[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        fp[j] = __ldg(w + i + j * plane + s);
+        f0[j] = __ldg(w + i + j * plane);
+        fm[j] = __ldg(w + i + j * plane - s);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[i + j * plane] = second_inner<T>(fp[j], f0[j], fm[j], hh);
+    }
+  }
+  for (; z < c.z1; ++z) {
+    const int64_t i = i0 + (int64_t)(z - c.z0) * plane;
+    out[i] = second_at<T>(w + i, cc, n, s, hh);
+  }
+}
+
+// d2w/dz2: the column's window w[z-1], w[z], w[z+1] stays in registers.
+template <typename T>
+__global__ void __launch_bounds__(kTileX * kTileY) k_second_z(const T* __restrict__ w, T* __restrict__ out, int nx,
+                                                              int ny, int nz, int zchunk, Den<T> hh) {
+  const Column c = column(nx, ny, nz, zchunk);
+  if (!c.ok) return;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t col = (int64_t)c.y * nx + c.x;
+  int za = c.z0, zb = c.z1;  // the slice's interior planes [za, zb)
+  if (za == 0) {             // the four-point ends
+    out[col] = second_at<T>(w + col, 0, nz, plane, hh);
+    za = 1;
+  }
+  if (zb == nz) {
+    out[col + (int64_t)(nz - 1) * plane] = second_at<T>(w + col + (int64_t)(nz - 1) * plane, nz - 1, nz, plane, hh);
+    zb = nz - 1;
+  }
+  if (za >= zb) return;
+  const T* p = w + col + (int64_t)za * plane;
+  T* q = out + col + (int64_t)za * plane;
+  T wm = __ldg(p - plane), w0 = __ldg(p);
+  int z = za;
+  for (; z + 4 <= zb; z += 4) {  // the next 4 planes' loads in flight together
+    const int64_t o = (int64_t)(z - za) * plane;
+    T wp[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wp[j] = __ldg(p + o + (j + 1) * plane);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      q[o + j * plane] = second_inner<T>(wp[j], w0, wm, hh);
+      wm = w0;
+      w0 = wp[j];
+    }
+  }
+  for (; z < zb; ++z) {
+    const int64_t o = (int64_t)(z - za) * plane;
+    const T wp = __ldg(p + o + plane);
+    q[o] = second_inner<T>(wp, w0, wm, hh);
+    wm = w0;
+    w0 = wp;
   }
 }
 
@@ -117,10 +234,12 @@ Den<T> make_den(double h, int twice) {
   const T inv = (T)std::ldexp(1.0, 1 - e);  // 1 / d when d is a power of two
   D.pow2 = m == 0.5 && std::isfinite(inv) && inv != T(0);
   D.inv = D.pow2 ? inv : T(0);
+  D.k = 1 - e;
   return D;
 }
 
-int fd_grid(int64_t work) {
+// Grid of tiles, with z split so that about 16 CTAs per SM are launched.
+dim3 fd_grid(int nx, int ny, int nz, int* zchunk) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -128,37 +247,50 @@ int fd_grid(int64_t work) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms < 1) sms = 1;
   }
-  const int64_t cap = (int64_t)sms * 8;  // 8 blocks of 256 threads per SM, grid-stride beyond
-  return (int)(work < cap ? (work > 0 ? work : 1) : cap);
+  const int64_t tiles = (int64_t)((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY);
+  int64_t split = (16 * (int64_t)sms + tiles - 1) / tiles;
+  split = std::max<int64_t>(1, std::min<int64_t>(split, nz));
+  *zchunk = (int)((nz + split - 1) / split);
+  const int gz = (nz + *zchunk - 1) / *zchunk;
+  return dim3((unsigned)((nx + kTileX - 1) / kTileX), (unsigned)((ny + kTileY - 1) / kTileY), (unsigned)gz);
 }
 
 }  // namespace
 
 cudaError_t launch_fd_vorticity_z(int dtype, const void* u, const void* v, void* out, int64_t nx, int64_t ny,
                                   int64_t nz, double h, cudaStream_t st) {
-  const int64_t rows = ny * nz, work = rows * ((nx + kFdThreads - 1) / kFdThreads);
-  const int grid = fd_grid(work);
+  int zc = 1;
+  const dim3 grid = fd_grid((int)nx, (int)ny, (int)nz, &zc);
+  const dim3 block(kTileX, kTileY);
   if (dtype == 1)
-    k_vorticity_z<float><<<grid, kFdThreads, 0, st>>>((const float*)u, (const float*)v, (float*)out, nx, ny, rows,
-                                                      make_den<float>(h, 1));
+    k_vorticity_z<float><<<grid, block, 0, st>>>((const float*)u, (const float*)v, (float*)out, (int)nx, (int)ny,
+                                                 (int)nz, zc, make_den<float>(h, 1));
   else
-    k_vorticity_z<double><<<grid, kFdThreads, 0, st>>>((const double*)u, (const double*)v, (double*)out, nx, ny,
-                                                       rows, make_den<double>(h, 1));
+    k_vorticity_z<double><<<grid, block, 0, st>>>((const double*)u, (const double*)v, (double*)out, (int)nx, (int)ny,
+                                                  (int)nz, zc, make_den<double>(h, 1));
   return cudaGetLastError();
 }
 
 cudaError_t launch_fd_second(int dtype, const void* w, void* out, int64_t nx, int64_t ny, int64_t nz, int axis,
                              double h, cudaStream_t st) {
-  const int64_t rows = ny * nz, work = rows * ((nx + kFdThreads - 1) / kFdThreads);
-  const int64_t n = axis == 0 ? nx : axis == 1 ? ny : nz;
-  const int64_t s = axis == 0 ? 1 : axis == 1 ? nx : nx * ny;
-  const int grid = fd_grid(work);
-  if (dtype == 1)
-    k_second<float><<<grid, kFdThreads, 0, st>>>((const float*)w, (float*)out, nx, ny, rows, axis, n, s,
+  int zc = 1;
+  const dim3 grid = fd_grid((int)nx, (int)ny, (int)nz, &zc);
+  const dim3 block(kTileX, kTileY);
+  if (dtype == 1) {
+    if (axis == 2)
+      k_second_z<float><<<grid, block, 0, st>>>((const float*)w, (float*)out, (int)nx, (int)ny, (int)nz, zc,
+                                                make_den<float>(h, 0));
+    else
+      k_second_xy<float><<<grid, block, 0, st>>>((const float*)w, (float*)out, (int)nx, (int)ny, (int)nz, zc, axis,
                                                  make_den<float>(h, 0));
-  else
-    k_second<double><<<grid, kFdThreads, 0, st>>>((const double*)w, (double*)out, nx, ny, rows, axis, n, s,
+  } else {
+    if (axis == 2)
+      k_second_z<double><<<grid, block, 0, st>>>((const double*)w, (double*)out, (int)nx, (int)ny, (int)nz, zc,
+                                                 make_den<double>(h, 0));
+    else
+      k_second_xy<double><<<grid, block, 0, st>>>((const double*)w, (double*)out, (int)nx, (int)ny, (int)nz, zc, axis,
                                                   make_den<double>(h, 0));
+  }
   return cudaGetLastError();
 }
 
