@@ -218,7 +218,10 @@ def e2e_two_streams(args, world, device, fields, hbufs, held, raw_bytes_step):
     import paper_2308_11759_gb300 as pcz
 
     names = list(fields)
-    streams = {n: torch.cuda.Stream(device=device) for n in names}
+    # the first field's pipeline at the higher priority: its retrievals (and
+    # the transfers they feed) are scheduled ahead of the second field's
+    # compression as CTAs drain, so the host link is busy while the SMs compress
+    streams = {n: torch.cuda.Stream(device=device, priority=(-1 if j == 0 else 0)) for j, n in enumerate(names)}
     pool = ThreadPoolExecutor(max_workers=len(names))  # the same host threads every step
 
     def pipeline(name):
