@@ -31,7 +31,8 @@ def _bits(a):
     return a.view(np.uint32 if a.dtype == np.float32 else np.uint64)
 
 
-SHAPES = [(37, 29, 45), (9, 130, 7), (3, 3, 3), (4, 5, 4), (50, 33), (3, 3)]
+# rows that are a multiple of 4 values long take the float32 vector kernel
+SHAPES = [(37, 29, 45), (9, 130, 7), (3, 3, 3), (4, 5, 4), (50, 33), (3, 3), (13, 20, 132), (5, 3, 4), (7, 11, 260)]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
@@ -57,6 +58,23 @@ def test_second_derivative_equals_oracle(P, dtype, h):
                 continue
             got = P.fd_second(wd, axis, h).cpu().numpy()
             assert np.array_equal(_bits(got), _bits(D.second(w, axis, h))), (shape, axis)
+
+
+def test_vector_and_scalar_vorticity_agree(P):
+    # the same float32 field through the vector kernel (16-byte aligned) and
+    # through the scalar one (arrays starting 4 bytes off alignment)
+    u = S.powerlaw((11, 17, 136), seed=900, dtype=np.float32)
+    v = S.powerlaw((11, 17, 136), seed=901, dtype=np.float32)
+    a = P.fd_vorticity_z(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), 0.5)
+    n = u.size
+    bu, bv, bo = (torch.empty(n + 1, device="cuda") for _ in range(3))
+    uo, vo, oo = bu[1:].view(u.shape), bv[1:].view(u.shape), bo[1:].view(u.shape)
+    uo.copy_(torch.from_numpy(u))
+    vo.copy_(torch.from_numpy(v))
+    P.fd_vorticity_z(uo, vo, 0.5, out=oo)
+    assert uo.data_ptr() % 16 != 0
+    assert torch.equal(a.view(torch.int32), oo.view(torch.int32))
+    assert np.array_equal(_bits(a.cpu().numpy()), _bits(D.vorticity_z(u, v, 0.5)))
 
 
 def test_large_field_sampled(P):
