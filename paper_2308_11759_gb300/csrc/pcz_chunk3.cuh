@@ -492,7 +492,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
             xtc[m] = xtn[m];
-            e[m] = en[m];
+            if constexpr (sizeof(T) == 8) e[m] = en[m];  // float32 recomputes it below
           }
         } else if (esc == 7 || pp == 0) {
           done = true;
@@ -596,9 +596,19 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       for (int m = 0; m < 4; ++m) {
         if (mode == kModeRaw) {
           xtc[m] = F::add(xt[m], eo[m]);
-          e[m] = F::sub(x[m], xtc[m]);
+          if constexpr (sizeof(T) == 8) e[m] = F::sub(x[m], xtc[m]);
         }
       }
+    }
+    if constexpr (sizeof(T) == 4) {
+      // float32: the next residual x - x~_i for every mode, recomputed here so
+      // that it is not live across the escalation loop (fewer spills; the
+      // same values: a passing brick's candidate residual was x - x~_i, and
+      // lanes outside the field are padded again at the next component).
+      // Float64 keeps the loop's value: a second FP64 subtraction costs more
+      // than the spills it saves.
+#pragma unroll
+      for (int m = 0; m < 4; ++m) e[m] = F::sub(x[m], xtc[m]);
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
