@@ -330,11 +330,12 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       if (line_in && m < nvx && not_finite<T>(x[m])) bad = true;
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(P.flags, kFlagNonFinite);
   }
-  // Algorithm 1 starts from x~ = 0; the first residual is x - 0
+  // Algorithm 1 starts from x~ = 0; the first residual is x - 0, which is x
+  // itself in IEEE arithmetic (-0 - +0 = -0), so no subtraction is issued
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     xt[m] = T(0);
-    e[m] = F::sub(x[m], T(0));
+    e[m] = x[m];
   }
   S* buf = bbuf + warp * 128;
   // buffer slots (each below 128) of this lane's line in each pass and of its
@@ -478,7 +479,10 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const T xi = normal ? Fmt<T>::val(dequantize_f64_normal(r[m], s)) : dequantize_val<T>(r[m], s);  // x_i = D(y_i)
-          xtn[m] = F::add(xt[m], xi);               // x~ + x_i (candidate)
+          // x~ + x_i (candidate); for the first component +0 + x_i, which is
+          // x_i with -0 turned to +0 -- a bit test instead of an FP64 add
+          const U xb = F::bits(xi);
+          xtn[m] = i == 0 ? F::val(xb == F::SIGN ? U(0) : xb) : F::add(xt[m], xi);
           en[m] = F::sub(x[m], xtn[m]);             // the next residual
           if (line_in && m < nvx && !within<T>(en[m], tb)) ok = false;
         }
