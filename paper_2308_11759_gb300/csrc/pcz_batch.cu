@@ -221,18 +221,21 @@ __host__ __device__ constexpr size_t batch_mixed_smem() {
 
 template <typename T>
 static int batch_mixed_grid_t() {
-  static int grid = 0;
-  if (!grid) {
+  // CTAs that fit on the GPU at once, queried once (thread-safe initialisation);
+  // also sets the kernel's shared-memory limit, which launches and graph
+  // captures need
+  static const int grid = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_batch_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_mixed_smem<T>());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_mixed<T>, kCompressThreads3,
-                                                      batch_mixed_smem<T>()) != cudaSuccess ||
-        per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_mixed<T>, kCompressThreads3, batch_mixed_smem<T>()) !=
+        cudaSuccess) {
+      cudaGetLastError();
       per = 1;
-    grid = (sms > 0 ? sms : 1) * per;
-  }
+    }
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }();
   return grid;
 }
 
@@ -249,36 +252,42 @@ cudaError_t launch_compress_batch_mixed(int dtype, const BatchParams* d_bp, int 
 
 template <typename T, int MINB>
 static int batch3_grid_t() {
-  static int grid = 0;
-  if (!grid) {
+  // CTAs that fit on the GPU at once, queried once (thread-safe initialisation);
+  // also sets the kernel's shared-memory limit, which launches and graph
+  // captures need
+  static const int grid = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_batch3<T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)compress_smem3<T>());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3<T, MINB>, kCompressThreads3,
-                                                      compress_smem3<T>()) != cudaSuccess ||
-        per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3<T, MINB>, kCompressThreads3, compress_smem3<T>()) !=
+        cudaSuccess) {
+      cudaGetLastError();
       per = 1;
-    grid = (sms > 0 ? sms : 1) * per;
-  }
+    }
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }();
   return grid;
 }
 
 template <typename T, int W>
 static int batch_small_grid_t() {
-  static int grid = 0;
-  if (!grid) {
+  // CTAs that fit on the GPU at once, queried once (thread-safe initialisation);
+  // also sets the kernel's shared-memory limit, which launches and graph
+  // captures need
+  static const int grid = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_batch_small<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)batch_small_smem<T, W>());
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_small<T, W>, 32 * W, batch_small_smem<T, W>()) !=
-            cudaSuccess ||
-        per < 1)
+        cudaSuccess) {
+      cudaGetLastError();
       per = 1;
-    grid = (sms > 0 ? sms : 1) * per;
-  }
+    }
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }();
   return grid;
 }
 

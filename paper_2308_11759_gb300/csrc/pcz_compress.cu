@@ -136,18 +136,18 @@ static cudaError_t launch_compress_t(const CompressParams& p, cudaStream_t s, bo
   const int use_tma = tma_staging() && device_field && make_brick_map<T>(p, row_box ? 128 : 4, &map) ? 1 : 0;
   int64_t grid = p.nchunks;
   if (use_tma) {  // persistent: the CTAs that fit at once
-    static int per_sm[2] = {0, 0}, sms = 0;
-    int& per = per_sm[sizeof(T) == 8];
-    if (!per) {
-      int dev = 0;
+    static const int64_t fit = [smem_tma] {  // once per type, thread-safe
+      int dev = 0, sms = 0, per = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_compress3_tma<T>, kCompressThreads3, smem_tma) !=
-              cudaSuccess ||
-          per < 1)
+          cudaSuccess) {
+        cudaGetLastError();
         per = 1;
-    }
-    grid = std::min<int64_t>(grid, (int64_t)per * std::max(sms, 1));
+      }
+      return (int64_t)std::max(per, 1) * std::max(sms, 1);
+    }();
+    grid = std::min<int64_t>(grid, fit);
   }
   if (use_tma)
     k_compress3_tma<T><<<(unsigned)grid, kCompressThreads3, smem_tma, s>>>(p, map, row_box);

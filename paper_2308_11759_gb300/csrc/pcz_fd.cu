@@ -302,13 +302,12 @@ Den<T> make_den(double h, int twice) {
 
 // Grid of tiles, with z split so that about 16 CTAs per SM are launched.
 dim3 fd_grid(int nx, int ny, int nz, int* zchunk) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {  // once, thread-safe
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms < 1) sms = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   const int64_t tiles = (int64_t)((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY);
   int64_t split = (16 * (int64_t)sms + tiles - 1) / tiles;
   split = std::max<int64_t>(1, std::min<int64_t>(split, nz));

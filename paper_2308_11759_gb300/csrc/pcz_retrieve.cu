@@ -705,21 +705,20 @@ int retrieve_unit_mult(int ncomp) {
 
 template <typename T>
 static int retrieve_grid_t(int64_t nunits) {
-  static int per_sm[2] = {0, 0};  // CTAs per SM that fit (queried once per type)
-  static int sms = 0;
-  int& ps = per_sm[sizeof(T) == 8];
-  if (!ps) {
-    int dev = 0;
+  // CTAs that fit on the GPU at once, queried once per type (a function-local
+  // static: initialised once even when several host threads get here first)
+  static const int64_t g = [] {
+    int dev = 0, sms = 0, ps = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_retrieve3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)retrieve_smem3<T>());
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_retrieve3<T>, kRThreads, retrieve_smem3<T>()) !=
-            cudaSuccess ||
-        ps < 1)
+        cudaSuccess) {
+      cudaGetLastError();
       ps = 1;
-    if (sms < 1) sms = 1;
-  }
-  const int64_t g = (int64_t)ps * sms;
+    }
+    return (int64_t)(ps < 1 ? 1 : ps) * (sms < 1 ? 1 : sms);
+  }();
   return (int)(nunits < g ? (nunits > 0 ? nunits : 1) : g);
 }
 
