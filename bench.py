@@ -351,25 +351,33 @@ def run_pcz(args, rank, world, device):
                           "gbs_algorithmic": round(alg[k] / (ms * 1e-3) / 1e9, 1) if k in alg and ms > 0 else None}
     launches = sum(n for _, n in ktimes.values())
 
-    # per field type: kernel times of one more step, from the library's events
+    # per field type: kernel times from the library's events, the median of
+    # args.kernel_reps launches each (outside the timed step)
     per_dtype = {}
+    reps = max(1, args.kernel_reps)
     for name, x in fields.items():
         st = held[name]
         fb = info[name]["field_bytes"]
         tau = [st.tau(i) for i in range(st.n)]
-        pcz.timing_enable(True)
-        st2 = pcz.compress(x, tau)
-        tc = pcz.timing_read()
+        cl = []
+        for _ in range(reps):
+            pcz.timing_enable(True)
+            st2 = pcz.compress(x, tau)
+            cl.append(pcz.timing_read()["compress"][0])
+            pcz.timing_enable(False)
+            st2.close()
         rms = []
         for k in range(1, N_COMP + 1):
-            pcz.timing_enable(True)
-            st2.retrieve(k=k, out=outs[name])
-            tr = pcz.timing_read()
-            rms.append(tr["retrieve"][0])
+            rl = []
+            for _ in range(reps):
+                pcz.timing_enable(True)
+                st.retrieve(k=k, out=outs[name])
+                rl.append(pcz.timing_read()["retrieve"][0])
+            rms.append(statistics.median(rl))
         pcz.timing_enable(False)
-        st2.close()
-        cms = tc["compress"][0]
+        cms = statistics.median(cl)
         per_dtype[name] = {"compress_ms": round(cms, 3), "compress_gbs": round(fb / (cms * 1e-3) / 1e9, 2),
+                           "launches_per_median": reps,
                            "compress_roofline_frac": round(info[name]["compress_bytes"] / (cms * 1e-3) / 1e9 / hbm, 5),
                            "retrieve_ms_per_k": [round(v, 3) for v in rms],
                            "retrieve_gbs": round(N_COMP * fb / (sum(rms) * 1e-3) / 1e9, 2),
@@ -1006,6 +1014,7 @@ def main():
     ap.add_argument("--serve-size", type=int, default=256)
     ap.add_argument("--no-configs", action="store_true", help="skip the 64^3 and 1024^3 configuration legs")
     ap.add_argument("--no-use-case", action="store_true", help="skip the derivatives-of-reconstructions leg")
+    ap.add_argument("--kernel-reps", type=int, default=20, help="launches per median in the per-type kernel times")
     ap.add_argument("--c5-size", type=int, default=1024)
     ap.add_argument("--c5-queries", type=int, default=2000)
     args = ap.parse_args()
