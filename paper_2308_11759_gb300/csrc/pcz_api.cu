@@ -5,10 +5,10 @@
 // Every step of the method runs in the kernels (pcz_compress.cu,
 // pcz_retrieve.cu, pcz_misc.cu); this file only moves sizes, pointers and
 // per-component metadata (tolerances, Sec. 6.2) around them.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
