@@ -77,6 +77,11 @@ CASES = [
     # 1D bricks that escalate (every third brick; stored inputs), mixed with random bricks
     ("esc1d_f32", lambda: _esc1d(0, 257, 50)[0], lambda: _esc1d(0, 257, 50)[1], 2),
     ("esc1d_f64", lambda: _esc1d(3, 257, 51)[0], lambda: _esc1d(3, 257, 51)[1], 2),
+    # the largest component count (PC_MAX_COMPONENTS = 64, tau_i = 2^-i range): retrieval in
+    # 8 rounds of 8 components, the late components lossless or ZERO
+    ("max64_f64_bin1", lambda: S.powerlaw((14, 13, 11), seed=23, dtype=np.float64), "bin1", 64),
+    ("max64_f32_bin1", lambda: S.powerlaw((14, 13, 11), seed=24, dtype=np.float32), "bin1", 64),
+    ("max64_2d_f32_bin1", lambda: S.powerlaw((37, 29), seed=25, dtype=np.float32), "bin1", 64),
 ]
 
 
@@ -138,8 +143,8 @@ def _tau(x, kind, n):
     if kind is None:
         return [1.0 / (i + 1) for i in range(n)]
     r = O.value_range(x)
-    if kind == "bin8":
-        return O.tau_binary(r, 8, n)
+    if kind in ("bin1", "bin8"):
+        return O.tau_binary(r, int(kind[3:]), n)
     return O.tau_binary(r, 4, n) if kind == "bin4" else O.tau_decade(r, n)
 
 
@@ -151,7 +156,7 @@ def pair(request, P):
     xd = torch.from_numpy(x).cuda()
     if isinstance(kind, str):  # the product's own schedule from the device range is the oracle's, bit for bit
         if kind.startswith("bin"):
-            gt = P.field_tau_schedule(xd, "binary", n, param={"bin4": 4, "bin8": 8}[kind])
+            gt = P.field_tau_schedule(xd, "binary", n, param=int(kind[3:]))
         else:
             gt = P.field_tau_schedule(xd, "decade", n)
         assert gt == tau
