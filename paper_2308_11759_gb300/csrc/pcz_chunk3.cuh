@@ -374,18 +374,15 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       if (line_in && m < nvx && !within<T>(e[m], tb)) small = false;
     const unsigned big_votes = __ballot_sync(FULL, !small);
     const bool zero_blk = !have || ((big_votes & HALF) == 0u);
-    bool nf = false;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) nf |= not_finite<T>(e[m]);
-    const unsigned nf_votes = __ballot_sync(FULL, nf);
-    const bool raw_forced = !zero_blk && ((nf_votes & HALF) != 0u);
-
-    // R6: block exponent and exact quantisation
+    // R6: block exponent and exact quantisation.  The largest biased exponent
+    // of the brick is also its finiteness test: an infinite or NaN residual
+    // (all-ones exponent) forces RAW.
     int be = 0;
 #pragma unroll
     for (int m = 0; m < 4; ++m) be = max(be, biased_exp<T>(F::bits(e[m])));
 #pragma unroll
     for (int o = 8; o >= 1; o >>= 1) be = max(be, __shfl_xor_sync(FULL, be, o));
+    const bool raw_forced = !zero_blk && be == (1 << F::EXPW) - 1;
     const int emax = block_emax_from_be<T>(be);
     const int s = Q - emax;
     S q[4];
@@ -617,16 +614,23 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       if (line_in && m < nvx) {
-        if (!within<T>(e[m], tb)) ++viol;
         const U a = F::bits(e[m]) & F::ABS;
         merr = a > merr ? a : merr;
       }
     }
 #pragma unroll
     for (int o = 8; o >= 1; o >>= 1) {
-      viol += __shfl_xor_sync(FULL, viol, o);
       const U y = (U)__shfl_xor_sync(FULL, (typename std::conditional<sizeof(U) == 8, unsigned long long, unsigned>::type)merr, o);
       merr = y > merr ? y : merr;
+    }
+    // failures are counted only where a brick of the warp is RAW (a CODED or
+    // ZERO brick meets tau_i on every value by construction)
+    if (__any_sync(FULL, have && mode == kModeRaw)) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if (line_in && m < nvx && !within<T>(e[m], tb)) ++viol;
+#pragma unroll
+      for (int o = 8; o >= 1; o >>= 1) viol += __shfl_xor_sync(FULL, viol, o);
     }
 
     const int par = (i & 1) * 32;
