@@ -212,14 +212,14 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
         for (int ii = 0; ii < 4; ++ii)
           if (j >= nvy) e[ii + 4 * j] = e[ii + 4 * (j - 1)];
     }
-    bool small = true, nf = false;
+    bool small = true;
     int be = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       if ((k & 3) < nvx && (k >> 2) < nvy && !within<T>(e[k], tb)) small = false;
-      nf |= not_finite<T>(e[k]);
       be = max(be, biased_exp<T>(F::bits(e[k])));
     }
+    const bool nf = be == (1 << F::EXPW) - 1;  // an infinite or NaN residual: all-ones exponent
     const bool zero_blk = !have || small;  // R5
     int mode = kModeZero, esc = 0, p = 0, len = 2;
     const int emax = block_emax_from_be<T>(be);
@@ -315,10 +315,17 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
     int se = (have && mode == kModeCoded) ? esc : 0;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
-      se += __shfl_xor_sync(FULL, se, o);
-      viol += __shfl_xor_sync(FULL, viol, o);
       const unsigned long long y = __shfl_xor_sync(FULL, merr, o);
       merr = y > merr ? y : merr;
+    }
+    // escalations and Eq. 1 failures (RAW bricks only) are rare: summed only
+    // where a lane has some
+    if (__any_sync(FULL, se != 0 || viol != 0)) {
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        se += __shfl_xor_sync(FULL, se, o);
+        viol += __shfl_xor_sync(FULL, viol, o);
+      }
     }
     if (have) {
       P.brick_len[(int64_t)i * P.nbricks + b] = (uint16_t)len;
