@@ -58,15 +58,18 @@ TRAFFIC = {"retrieve": 1291889936}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over the 16 retrieval launches "
                   "(k = 1..8, float32 and float64) of this workload at 512^3")
 INSTRUCTIONS = {"retrieve": 2051047084}
-# Pipe utilisation (ncu --set full on the 320^3 case of this workload, current kernels): the
-# retrieval (k = 8) and compression kernels are bound by instruction issue, not by HBM.
+# Pipe utilisation (ncu --set full on the 320^3 case of this workload): the retrieval (k = 8)
+# and compression kernels are bound by instruction issue, not by HBM.  The retrieval figures
+# are of the current kernel; compression has since dropped a warp vote and some FP64
+# operations (2-4 % less time), its figures are of the kernel before that.
 PIPES = {"launch": "320^3, retrieval at k = 8, compression of 8 components",
          "retrieve": {"alu": {"f32": 0.569, "f64": 0.574}, "fp64": {"f32": 0.0, "f64": 0.662},
                       "issue_active": {"f32": 0.677, "f64": 0.604}},
          "compress": {"alu": {"f32": 0.708, "f64": 0.598}, "fp64": {"f32": 0.0, "f64": 0.464},
                       "issue_active": {"f32": 0.762, "f64": 0.584}},
          "source": "ncu sm__inst_executed_pipe_{alu,fp64}.avg.pct_of_peak_sustained_active, "
-                   "smsp__issue_active.avg.pct_of_peak_sustained_active"}
+                   "smsp__issue_active.avg.pct_of_peak_sustained_active; compression figures from the "
+                   "kernel before its last change (2-4 % less time since)"}
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
                   "384x384x256 (not multiples of 4), half sums of Gaussians and half k^-5/3 spectra, 6 components "
                   "(tau_i = 1e-(i+1) * range)")
