@@ -380,8 +380,11 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     int be = 0;
 #pragma unroll
     for (int m = 0; m < 4; ++m) be = max(be, biased_exp<T>(F::bits(e[m])));
-#pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) be = max(be, __shfl_xor_sync(FULL, be, o));
+    {  // the maximum over each brick's 16 lanes: two warp reductions (redux)
+      const unsigned lo = __reduce_max_sync(FULL, h ? 0u : (unsigned)be);
+      const unsigned hi = __reduce_max_sync(FULL, h ? (unsigned)be : 0u);
+      be = (int)(h ? hi : lo);
+    }
     const bool raw_forced = !zero_blk && be == (1 << F::EXPW) - 1;
     const int emax = block_emax_from_be<T>(be);
     const int s = Q - emax;
@@ -618,10 +621,16 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
         merr = a > merr ? a : merr;
       }
     }
+    if constexpr (sizeof(U) == 4) {  // per brick half: two warp reductions (redux)
+      const unsigned lo = __reduce_max_sync(FULL, h ? 0u : (unsigned)merr);
+      const unsigned hi = __reduce_max_sync(FULL, h ? (unsigned)merr : 0u);
+      merr = (U)(h ? hi : lo);
+    } else {
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) {
-      const U y = (U)__shfl_xor_sync(FULL, (typename std::conditional<sizeof(U) == 8, unsigned long long, unsigned>::type)merr, o);
-      merr = y > merr ? y : merr;
+      for (int o = 8; o >= 1; o >>= 1) {
+        const U y = (U)__shfl_xor_sync(FULL, (unsigned long long)merr, o);
+        merr = y > merr ? y : merr;
+      }
     }
     // failures are counted only where a brick of the warp is RAW (a CODED or
     // ZERO brick meets tau_i on every value by construction)
@@ -644,20 +653,17 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     __syncthreads();
     // chunk layout: every warp scans the 32 brick lengths for its own bricks'
     // offsets (no second barrier); warp 0 also records the chunk
+    // this warp's two bricks start after the lengths of the bricks before them:
+    // one warp sum (redux) over the lanes below 2 * warp
     const int l0 = s_len[par + lane];
-    int incl = l0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int offA = __shfl_sync(FULL, incl - l0, warp * 2), offB = __shfl_sync(FULL, incl - l0, warp * 2 + 1);
+    const int offA = (int)__reduce_add_sync(FULL, lane < 2 * warp ? (unsigned)l0 : 0u);
+    const int offB = offA + __shfl_sync(FULL, l0, 2 * warp);
     // chunk bookkeeping, spread so that no warp carries much more than the
     // others to the next barrier: warp 0 sizes the chunk and reserves its
     // pool space, warp 1 gathers the block counters, and each warp writes its
     // own bricks' index entries
     if (warp == 0) {
-      const int total = __shfl_sync(FULL, incl, 31);
+      const int total = (int)__reduce_add_sync(FULL, (unsigned)l0);
       const unsigned nw = (unsigned)((total + 63) >> 6);
       if (lane == 0) {
         s_cbits[i & 1] = total;
@@ -676,10 +682,15 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       unsigned long long me = s_merr[par + lane];
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
-        se += __shfl_xor_sync(FULL, se, o);
-        sv += __shfl_xor_sync(FULL, sv, o);
         const unsigned long long y = __shfl_xor_sync(FULL, me, o);
         me = y > me ? y : me;
+      }
+      if (__any_sync(FULL, se != 0 || sv != 0)) {  // escalations and failures are rare
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+          se += __shfl_xor_sync(FULL, se, o);
+          sv += __shfl_xor_sync(FULL, sv, o);
+        }
       }
       if (lane == 0) {
         const int64_t ci = (int64_t)i * P.nchunks + chunk;
