@@ -625,12 +625,10 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       const unsigned lo = __reduce_max_sync(FULL, h ? 0u : (unsigned)merr);
       const unsigned hi = __reduce_max_sync(FULL, h ? (unsigned)merr : 0u);
       merr = (U)(h ? hi : lo);
-    } else {
-#pragma unroll
-      for (int o = 8; o >= 1; o >>= 1) {
-        const U y = (U)__shfl_xor_sync(FULL, (unsigned long long)merr, o);
-        merr = y > merr ? y : merr;
-      }
+    } else {  // per brick half: the two halves' 64-bit maxima, four warp reductions
+      const unsigned long long lo = warp_max_u64(FULL, h ? 0ull : (unsigned long long)merr);
+      const unsigned long long hi = warp_max_u64(FULL, h ? (unsigned long long)merr : 0ull);
+      merr = (U)(h ? hi : lo);
     }
     // failures are counted only where a brick of the warp is RAW (a CODED or
     // ZERO brick meets tau_i on every value by construction)
@@ -679,12 +677,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
       const unsigned cc = __popc(__ballot_sync(FULL, md == kModeCoded));
       const unsigned cr = __popc(__ballot_sync(FULL, md == kModeRaw));
       int se = s_esc[par + lane], sv = s_viol[par + lane];
-      unsigned long long me = s_merr[par + lane];
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(FULL, me, o);
-        me = y > me ? y : me;
-      }
+      const unsigned long long me = warp_max_u64(FULL, s_merr[par + lane]);
       if (__any_sync(FULL, se != 0 || sv != 0)) {  // escalations and failures are rare
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {

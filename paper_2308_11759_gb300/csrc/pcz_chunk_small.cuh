@@ -313,15 +313,10 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
     const unsigned cc = __popc(__ballot_sync(FULL, have && mode == kModeCoded));
     const unsigned cr = __popc(__ballot_sync(FULL, have && mode == kModeRaw));
     int se = (have && mode == kModeCoded) ? esc : 0;
-    if constexpr (sizeof(T) == 4) {  // 32-bit patterns: one warp reduction (redux)
+    if constexpr (sizeof(T) == 4)  // 32-bit patterns: one warp reduction (redux)
       merr = __reduce_max_sync(FULL, (unsigned)merr);
-    } else {
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(FULL, merr, o);
-        merr = y > merr ? y : merr;
-      }
-    }
+    else
+      merr = warp_max_u64(FULL, merr);
     // escalations and Eq. 1 failures (RAW bricks only) are rare: summed only
     // where a lane has some
     if (__any_sync(FULL, se != 0 || viol != 0)) {

@@ -390,6 +390,15 @@ __device__ __forceinline__ uint64_t peek64(const uint64_t* __restrict__ w, uint6
   return (a >> sh) | (b << (64 - sh));
 }
 
+// The largest 64-bit value over the lanes of `mask` (every lane of it calls):
+// the largest high word, then the largest low word among the lanes that hold
+// it -- two warp reductions (redux) instead of a shuffle ladder.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned mask, unsigned long long v) {
+  const unsigned hi = __reduce_max_sync(mask, (unsigned)(v >> 32));
+  const unsigned lo = __reduce_max_sync(mask, (unsigned)(v >> 32) == hi ? (unsigned)v : 0u);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
 __device__ __forceinline__ uint64_t low_mask64(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1); }
 
 // ---------------------------------------------------------------------------
