@@ -34,6 +34,7 @@ exchange (bricks are independent), so there is no collective beyond the
 timing barrier.
 """
 import argparse
+import gc
 import json
 import math
 import os
@@ -255,12 +256,15 @@ def e2e_two_streams(args, world, device, fields, hbufs, held, raw_bytes_step):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    gc.collect()
+    gc.disable()
     marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     marks[0].record()
     for i in range(args.steps):
         step()
         marks[i + 1].record()
     torch.cuda.synchronize()
+    gc.enable()
     pool.shutdown()
     ems = max_over_ranks(marks[0].elapsed_time(marks[-1]), world, device)
     return {"value": round(job_gbs(world, raw_bytes_step, args.steps, ems), 3), "unit": "GB/s",
@@ -321,6 +325,8 @@ def run_pcz(args, rank, world, device):
     torch.cuda.synchronize()
     pcz.timing_enable(True)
     sampler.start()
+    gc.collect()
+    gc.disable()  # no collector pauses inside the timed steps (the host is on the steps' critical path)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
@@ -328,6 +334,7 @@ def run_pcz(args, rank, world, device):
         step()
     t1.record()
     torch.cuda.synchronize()
+    gc.enable()
     clocks = sampler.stop()
     ktimes = pcz.timing_read()
     pcz.timing_enable(False)
@@ -447,6 +454,8 @@ def run_pcz(args, rank, world, device):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        gc.collect()
+        gc.disable()
         a = time.perf_counter()
         marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         marks[0].record()
@@ -455,6 +464,7 @@ def run_pcz(args, rank, world, device):
             marks[i + 1].record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - a
+        gc.enable()
         ems = max_over_ranks(marks[0].elapsed_time(marks[-1]), world, device)
         h2d = sum(v["field_bytes"] for v in info.values())
         d2h = sum(v["field_bytes"] * N_COMP for v in info.values())
