@@ -148,11 +148,28 @@ def test_host_buffers(P):
     assert P.field_range(xp) == P.field_range(torch.from_numpy(x).cuda())
     op = torch.empty(x.shape, dtype=torch.float32).pin_memory()
     pinned.retrieve(k=3, out=op)
+    torch.cuda.synchronize()  # pinned results are complete in stream order
     assert torch.equal(op.view(torch.uint8), dev.retrieve(k=3).cpu().view(torch.uint8))
     acc = torch.empty(x.shape, dtype=torch.float32).pin_memory()
     pinned.retrieve(k=2, out=acc)
     pinned.refine(2, 5, acc)  # x~_2 read from and x~_5 written to pinned memory
+    torch.cuda.synchronize()
     assert torch.equal(acc.view(torch.uint8), dev.retrieve(k=5).cpu().view(torch.uint8))
+    # 2D and 1D fields: pinned input and output (written in place by the kernel), pageable output
+    for shape, dt in (((130, 97), np.float64), ((4099,), np.float32)):
+        y = S.powerlaw(shape, seed=36, dtype=dt)
+        t = O.tau_decade(O.value_range(y), 6)
+        d = P.compress(torch.from_numpy(y).cuda(), t)
+        h = P.compress(torch.from_numpy(y).pin_memory(), t)
+        assert h.serialize() == d.serialize()
+        want = d.retrieve(k=4).cpu()
+        o1 = torch.empty(want.shape, dtype=want.dtype).pin_memory()
+        h.retrieve(k=4, out=o1)
+        o2 = np.empty(shape, dtype=dt)
+        h.retrieve(k=4, out=o2)  # pageable: returns with the data in place
+        torch.cuda.synchronize()
+        assert torch.equal(o1.view(torch.uint8), want.view(torch.uint8))
+        assert np.array_equal(o2.view(np.uint8), want.numpy().view(np.uint8))
 
 
 def test_error_statuses(P):
