@@ -847,6 +847,20 @@ def run_use_case(args, device):
                        "algorithmic_bytes": nbytes}
         kern[name] = res
         del u, v, w, out
+    # the oracle (numpy, one host thread) on the same float64 fields, beside the kernels
+    from oracle import derivatives as D
+
+    hu, hv, hw = (c.cpu().numpy() for c in vel)
+    t = time.perf_counter()
+    D.vorticity_z(hu, hv)
+    t_om = time.perf_counter() - t
+    t = time.perf_counter()
+    D.second(hw, 2)
+    t_wzz = time.perf_counter() - t
+    nb = hu.nbytes
+    kern["oracle_f64"] = {"vorticity_z": {"ms": round(1e3 * t_om, 1), "gbs": round(3 * nb / t_om / 1e9, 3)},
+                          "w_zz": {"ms": round(1e3 * t_wzz, 1), "gbs": round(2 * nb / t_wzz / 1e9, 3)},
+                          "cores": 1, "kind": "oracle (numpy)"}
     return {"workload": "3 float64 components of 384 x 384 x 256 (k^-5/3, std 4), tau = 1, 2^-4, 2^-9, h = 1",
             "per_k": per_k, "vorticity_max": round(om_max, 4), "w_zz_max": round(wzz_max, 4),
             "kernels": kern, "bound": "hbm (algorithmic bytes: inputs read once, output written once)"}
