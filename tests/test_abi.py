@@ -108,3 +108,28 @@ def test_tau_schedules_on_the_host(L):
     assert L.pc_tau_schedule(P.PC_TAU_BINARY, 1.0, 0, 4, out) == 1
     assert L.pc_tau_schedule(7, 1.0, 4, 4, out) == 1
     assert L.pc_tau_schedule(P.PC_TAU_DECADE, 1.0, 2, 0, out) == 1
+
+
+def test_derivative_argument_errors_without_device_work(L):
+    """pc_fd_vorticity_z / pc_fd_second refuse bad shapes, axes and spacings
+    with PC_ERR_ARG before any device work (and host pointers after it)."""
+    d3 = (C.c_int64 * 3)(8, 8, 8)
+    d1 = (C.c_int64 * 1)(8)
+    small = (C.c_int64 * 3)(8, 2, 8)  # ny = 2
+    buf = (C.c_float * 512)()
+    p = C.cast(buf, C.c_void_p)
+    vort = L.pc_fd_vorticity_z
+    vort.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_double, C.c_void_p,
+                     C.c_void_p]
+    sec = L.pc_fd_second
+    sec.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]
+    assert vort(p, p, d1, 1, 1, 1.0, p, None) == 1  # v_x - u_y needs two dimensions
+    assert vort(p, p, small, 3, 1, 1.0, p, None) == 1  # and three points along y
+    assert vort(p, p, d3, 3, 1, 0.0, p, None) == 1  # h must be positive
+    assert vort(p, p, d3, 3, 1, float("nan"), p, None) == 1
+    assert vort(p, p, d3, 3, 3, 1.0, p, None) == 1  # bad dtype
+    assert vort(p, p, d3, 3, 1, 1.0, p, None) == 1  # host memory
+    assert sec(p, d3, 3, 1, 3, 1.0, p, None) == 1  # axis beyond the field
+    assert sec(p, (C.c_int64 * 3)(8, 8, 3), 3, 1, 2, 1.0, p, None) == 1  # 3 points along z
+    assert sec(p, d3, 0, 1, 0, 1.0, p, None) == 1  # ndims
+    assert b"" != L.pc_last_error()
