@@ -18,7 +18,9 @@
 // thread walks its column through a slice of z, so no index is divided per
 // value and a second derivative along z keeps its three-point window in
 // registers (each value loaded once).  Neighbours along x and y come from
-// L1/L2.  Each input is read from DRAM about once and the output written
+// L1/L2 (float32 rows of a multiple of 4 values: the vorticity kernel moves
+// float4s, 128-value tiles, x-neighbours by shuffle).  Each input is read from
+// DRAM about once and the output written
 // once: the kernels are bound by memory -- for float64 on GB300, whose FP64
 // rate is low, by the FP64 pipe, which is why powers of two scale the
 // exponent field with integer instructions where the result stays normal
