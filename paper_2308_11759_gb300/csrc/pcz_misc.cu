@@ -88,7 +88,12 @@ __device__ __forceinline__ void scan_segment(const uint32_t* __restrict__ in, ui
   if (tid == 0 && maxerr_out) *maxerr_out = merr_s;
 }
 
-// Components of one field: segment c is chunks [c * nchunks, (c + 1) * nchunks).
+// Components of one field, chunk tiles side by side: CTA (t, c) scans tile t
+// (4096 chunks) of component c.  Its base -- the words of the component's
+// chunks before the tile -- is a block reduction over those counts (read again,
+// from L2), so the tiles need no order among them; the block counters and the
+// largest error are accumulated with atomics into outputs cleared before the
+// launch, and the last tile writes the component's total.
 __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __restrict__ nwords,
                                                                uint64_t* __restrict__ word_off,
                                                                uint64_t* __restrict__ totals,
@@ -97,9 +102,82 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint32_t* __
                                                                const uint64_t* __restrict__ chunk_maxerr,
                                                                unsigned long long* __restrict__ maxerr,
                                                                int64_t nchunks) {
-  const int64_t c0 = (int64_t)blockIdx.x * nchunks;
-  scan_segment(nwords + c0, word_off + c0, chunk_counts + c0 * 5, chunk_maxerr ? chunk_maxerr + c0 : nullptr,
-               nchunks, totals + blockIdx.x, counts + 5 * blockIdx.x, maxerr ? maxerr + blockIdx.x : nullptr);
+  constexpr int64_t kTile = (int64_t)kScanThreads * kScanItems;
+  __shared__ uint64_t warp_sums[32];
+  const int comp = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = (int64_t)comp * nchunks, t0 = (int64_t)blockIdx.x * kTile;
+  const uint32_t* in = nwords + c0;
+  // the base: a block sum of the counts before the tile
+  uint64_t part = 0;
+  for (int64_t c = tid; c < t0; c += kScanThreads) part += in[c];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) warp_sums[warp] = part;
+  __syncthreads();
+  uint64_t base = 0;
+  if (warp == 0) {
+    base = warp_sums[lane];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) base += __shfl_xor_sync(0xffffffffu, base, o);
+  }
+  __syncthreads();  // warp_sums is reused below
+  if (tid == 0) warp_sums[0] = base;
+  __syncthreads();
+  base = warp_sums[0];
+  __syncthreads();
+  // the tile: an exclusive block scan from the base
+  const int64_t first = t0 + (int64_t)tid * kScanItems;
+  uint64_t v[kScanItems], local = 0;
+  unsigned my_cnt[5] = {0, 0, 0, 0, 0};
+  unsigned long long my_merr = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const int64_t c = first + q;
+    v[q] = c < nchunks ? in[c] : 0u;
+    local += v[q];
+    if (c < nchunks) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) my_cnt[k] += chunk_counts[(c0 + c) * 5 + k];
+      if (chunk_maxerr) my_merr = chunk_maxerr[c0 + c] > my_merr ? chunk_maxerr[c0 + c] : my_merr;
+    }
+  }
+  uint64_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t ws = warp_sums[lane];
+    uint64_t wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    warp_sums[lane] = wi - ws;  // exclusive over warps
+  }
+  __syncthreads();
+  uint64_t run = base + warp_sums[warp] + (incl - local);
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const int64_t c = first + q;
+    if (c < nchunks) word_off[c0 + c] = run;
+    run += v[q];
+  }
+  // counters and the largest error of the tile, then the component's total
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {  // a warp's share fits 32 bits: at most 128 chunks of 32 bricks
+    const unsigned x = __reduce_add_sync(0xffffffffu, my_cnt[k]);
+    if (lane == 0 && x) atomicAdd(&counts[5 * comp + k], (unsigned long long)x);
+  }
+  if (maxerr) {
+    const unsigned long long m = warp_max_u64(0xffffffffu, my_merr);
+    if (lane == 0 && m) atomicMax(&maxerr[comp], m);
+  }
+  if (blockIdx.x == gridDim.x - 1 && tid == kScanThreads - 1) totals[comp] = run;
 }
 
 // Segments of a batch of fields, described in device memory (so that a
@@ -206,8 +284,14 @@ cudaError_t launch_scan_chunks(const uint32_t* nwords, uint64_t* word_off, uint6
                                const uint64_t* chunk_maxerr, unsigned long long* maxerr, int n, int64_t nchunks,
                                cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_scan_chunks<<<n, kScanThreads, 0, s>>>(nwords, word_off, totals, chunk_counts, counts, chunk_maxerr, maxerr,
-                                           nchunks);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 5 * (size_t)n, s);
+  if (e == cudaSuccess && nchunks <= 0) return cudaMemsetAsync(totals, 0, sizeof(uint64_t) * (size_t)n, s);
+  if (e == cudaSuccess && maxerr) e = cudaMemsetAsync(maxerr, 0, sizeof(unsigned long long) * (size_t)n, s);
+  if (e != cudaSuccess) return e;
+  const int64_t tile = (int64_t)kScanThreads * kScanItems;
+  const dim3 grid((unsigned)((nchunks + tile - 1) / tile), (unsigned)n);
+  k_scan_chunks<<<grid, kScanThreads, 0, s>>>(nwords, word_off, totals, chunk_counts, counts, chunk_maxerr, maxerr,
+                                              nchunks);
   return cudaGetLastError();
 }
 
