@@ -290,6 +290,24 @@ __device__ __forceinline__ void dequantize_line(const typename Fmt<T>::S* q, int
   }
 }
 
+// R13 for a float64 coefficient decoded in 32-bit integers in units of 2^e:
+// the coefficient is q = r * 2^e exactly, |r| < 2^31, and 1 <= |q| < 2^63 when
+// r != 0.  For s in [-960, 1022] the result q * 2^-s is then normal and finite
+// (the bound of dequantize_line), so no rounding is needed: with |r|'s leading
+// one moved to bit 31, the 31 bits below it are the top of the 52-bit
+// fraction, and the biased exponent is 1023 + (31 - clz|r|) + e - s.  Pass
+// eb = (1053 + e - s) << 20 (that exponent minus 1, plus clz|r|, in the high
+// word's exponent field; the leading one, added at bit 20, completes it).
+// r = 0 gives +0.  Integer instructions only: no int -> double conversion,
+// whose FP64 pipe the partial-sum adds keep busy.
+__device__ __forceinline__ double scaled_i32_to_f64(int32_t r, uint32_t eb) {
+  const uint32_t a = (uint32_t)abs(r);
+  const uint32_t z = (uint32_t)__clz(a);
+  const uint32_t n = __funnelshift_l(0u, a, z);  // |r| << clz; 0 for r = 0
+  const uint32_t hw = ((n >> 11) + eb - (z << 20)) | ((uint32_t)r & 0x80000000u);
+  return __hiloint2double(a ? (int)hw : 0, (int)(n << 21));
+}
+
 // |e| <= tau on bit patterns: tb is the pattern of the largest T value not
 // above tau, so the comparison is exact; NaN and +-inf fail it.
 template <typename T>

@@ -28,7 +28,12 @@
 // p + 32) of both bricks, a 32x32 bit transpose across the warp turns planes
 // back into each lane's coefficients t + 16j, and the inverse reorder,
 // lifting and scaling run through a bank-conflict-free brick buffer; x_j is
-// then added into x~, component by component in ascending order.
+// then added into x~, component by component in ascending order.  Float64
+// pairs whose coded planes span fewer than 16 (most of them at tolerances a
+// few decades apart) are decoded in 32-bit integers scaled to their lowest
+// plane and converted to double without the FP64 pipe, which the partial-sum
+// adds keep busy; this form is a second instantiation of the kernel, used
+// when a brick decodes at least 3 components.
 #include <type_traits>
 
 #include "pcz_device.cuh"
@@ -328,8 +333,9 @@ __device__ __forceinline__ void start_sum(const BoxJob& J, int write, const Bric
 
 // Rebuilds one component of the warp's brick pair (lanes 0-15: brick A,
 // 16-31: brick B) from the parsed blocks mA/mB (slots sA/sB, spill pA/pB):
-// returns this lane's 4 values of x_j.
-template <typename T>
+// returns this lane's 4 values of x_j.  SC (float64): pairs whose coded
+// planes span fewer than 16 take the 32-bit integer decoding.
+template <typename T, bool SC>
 __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMeta& mB, const uint64_t* sA,
                                              const uint64_t* sB, const uint64_t* pA, const uint64_t* pB,
                                              const CompDesc* cd, typename Fmt<T>::S* buf, const int* ix,
@@ -354,76 +360,135 @@ __device__ __forceinline__ void rebuild_pair(const BlockMeta& mA, const BlockMet
     };
     const int lo = min((int)mA.p, (int)mB.p);
     const int hi = max((int)mA.top, (int)mB.top);
-    U u[4];
-    if (hi - lo < 16) {
-      // every coded plane of the pair lies in [lo, lo + 16): one transpose
-      // carries two coefficient groups, rows 0-15 the planes of group 2t and
-      // rows 16-31 those of group 2t + 1 (lane l fetches plane lo + (l & 15))
+    S r[4];            // the coefficients after the inverse transform
+    bool conv = true;  // r still to be dequantised into xi
+    bool scaled = false;
+    if constexpr (WIDE && SC) scaled = hi - lo < 16 && lo >= 6 && hi <= 58;
+    if (scaled) {
+      // 64-bit coefficients whose coded planes lie in [lo, lo + 16), lo >= 6,
+      // below plane 59, decoded in 32-bit integers in units of 2^(lo - 6).  A
+      // coefficient with negabinary digits v from plane lo is
+      // ((v ^ M) - M) * 2^lo with M = NBM >> lo (M's bits above v's do not
+      // matter).  In these units each pass of the inverse lifting turns
+      // multiples of 2^a into multiples of 2^(a - 2), so from 2^6 every shift
+      // divides an even number exactly; and |value| < 2^(hi - lo + 6.42) *
+      // 2.75^3 < 2^26 (2.75: the largest row sum of the inverse lifting's
+      // coefficients), while the unscaled value stays below 2^(hi + 4.8) <= 2^63.
+      // Neither form wraps, so the result is the 64-bit decoding's exactly.
       const int pl = lo + (lane & 15);
       const uint64_t WA = fetch(mA, sA, pA, pl), WB = fetch(mB, sB, pB, pl);
-      const uint32_t sel = h ? 0x7632u : 0x5410u;  // 16-bit group 2 t2 + h of both words
+      const uint32_t sel = h ? 0x7632u : 0x5410u;
+      const uint32_t M = (uint32_t)(F::NBM >> min(lo, 63));  // lo = 64: no digit at all
+      int32_t* b32 = reinterpret_cast<int32_t*>(buf);
 #pragma unroll
       for (int t2 = 0; t2 < 2; ++t2) {
         const uint32_t row = __byte_perm((uint32_t)(WA >> (32 * t2)), (uint32_t)(WB >> (32 * t2)), sel);
         const uint32_t w = transpose32(row, lane, tkeep);
-        u[2 * t2] = (U)((U)(w & 0xffffu) << lo);
-        u[2 * t2 + 1] = (U)((U)(w >> 16) << lo);
+        b32[ir[2 * t2]] = (int32_t)((((w & 0xffffu) ^ M) - M) << 6);
+        b32[ir[2 * t2 + 1]] = (int32_t)((((w >> 16) ^ M) - M) << 6);
+      }
+      __syncwarp();
+      {
+        int32_t a = b32[iz[0]], bq = b32[iz[1]], c = b32[iz[2]], d = b32[iz[3]];
+        lift_inv(a, bq, c, d);
+        b32[iz[0]] = a; b32[iz[1]] = bq; b32[iz[2]] = c; b32[iz[3]] = d;
+      }
+      __syncwarp();
+      {
+        int32_t a = b32[iy[0]], bq = b32[iy[1]], c = b32[iy[2]], d = b32[iy[3]];
+        lift_inv(a, bq, c, d);
+        b32[iy[0]] = a; b32[iy[1]] = bq; b32[iy[2]] = c; b32[iy[3]] = d;
+      }
+      __syncwarp();
+      int32_t q[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) q[m] = b32[ix[m]];
+      __syncwarp();
+      lift_inv(q[0], q[1], q[2], q[3]);
+      if (my.s >= -960 && my.s <= 1022) {  // R13 without rounding (scaled_i32_to_f64)
+        if constexpr (WIDE) {
+          if (my.mode == kModeCoded) {
+            const uint32_t eb = (uint32_t)(1053 + (lo - 6) - my.s) << 20;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xi[m] = scaled_i32_to_f64(q[m], eb);
+          }
+        }
+        conv = false;
+      } else {  // the general path below, on the unscaled coefficients
+#pragma unroll
+        for (int m = 0; m < 4; ++m) r[m] = (S)((U)(int64_t)q[m] << (lo - 6));
       }
     } else {
-      // lane l fetches plane base + l (and base + 32 + l for 64-bit
-      // coefficients when the coded planes of the pair span more than 32)
-      int base = 0;
-      bool two = WIDE;
-      if constexpr (WIDE) {
-        if (hi - lo < 32) {  // one 32-plane window holds every coded plane
-          base = lo;
-          two = false;
+      U u[4];
+      if ((!WIDE || !SC) && hi - lo < 16) {
+        // every coded plane of the pair lies in [lo, lo + 16): one transpose
+        // carries two coefficient groups, rows 0-15 the planes of group 2t and
+        // rows 16-31 those of group 2t + 1 (lane l fetches plane lo + (l & 15))
+        const int pl = lo + (lane & 15);
+        const uint64_t WA = fetch(mA, sA, pA, pl), WB = fetch(mB, sB, pB, pl);
+        const uint32_t sel = h ? 0x7632u : 0x5410u;  // 16-bit group 2 t2 + h of both words
+#pragma unroll
+        for (int t2 = 0; t2 < 2; ++t2) {
+          const uint32_t row = __byte_perm((uint32_t)(WA >> (32 * t2)), (uint32_t)(WB >> (32 * t2)), sel);
+          const uint32_t w = transpose32(row, lane, tkeep);
+          u[2 * t2] = (U)((U)(w & 0xffffu) << lo);
+          u[2 * t2 + 1] = (U)((U)(w >> 16) << lo);
+        }
+      } else {
+        // lane l fetches plane base + l (and base + 32 + l for 64-bit
+        // coefficients when the coded planes of the pair span more than 32)
+        int base = 0;
+        bool two = WIDE;
+        if constexpr (WIDE) {
+          if (hi - lo < 32) {  // one 32-plane window holds every coded plane
+            base = lo;
+            two = false;
+          }
+        }
+        const uint64_t WA0 = fetch(mA, sA, pA, base + lane), WB0 = fetch(mB, sB, pB, base + lane);
+        {
+          uint32_t tl[4];
+          tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
+          tl[1] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x7632);
+          tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
+          tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep) << base;
+        }
+        if constexpr (WIDE) {
+          if (two) {
+            const uint64_t WA1 = fetch(mA, sA, pA, lane + 32), WB1 = fetch(mB, sB, pB, lane + 32);
+            uint32_t th[4];
+            th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
+            th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
+            th[2] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x5410);
+            th[3] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x7632);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) u[j] |= (U)((uint64_t)transpose32(th[j], lane, tkeep) << 32);
+          }
         }
       }
-      const uint64_t WA0 = fetch(mA, sA, pA, base + lane), WB0 = fetch(mB, sB, pB, base + lane);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>(u[j]);
+      __syncwarp();
       {
-        uint32_t tl[4];
-        tl[0] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x5410);
-        tl[1] = __byte_perm((uint32_t)WA0, (uint32_t)WB0, 0x7632);
-        tl[2] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x5410);
-        tl[3] = __byte_perm((uint32_t)(WA0 >> 32), (uint32_t)(WB0 >> 32), 0x7632);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) u[j] = (U)transpose32(tl[j], lane, tkeep) << base;
+        S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
+        lift_inv(a, bq, c, d);
+        buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
       }
-      if constexpr (WIDE) {
-        if (two) {
-          const uint64_t WA1 = fetch(mA, sA, pA, lane + 32), WB1 = fetch(mB, sB, pB, lane + 32);
-          uint32_t th[4];
-          th[0] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x5410);
-          th[1] = __byte_perm((uint32_t)WA1, (uint32_t)WB1, 0x7632);
-          th[2] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x5410);
-          th[3] = __byte_perm((uint32_t)(WA1 >> 32), (uint32_t)(WB1 >> 32), 0x7632);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) u[j] |= (U)((uint64_t)transpose32(th[j], lane, tkeep) << 32);
-        }
+      __syncwarp();
+      {
+        S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
+        lift_inv(a, bq, c, d);
+        buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
       }
-    }
+      __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) buf[ir[j]] = nb_inv<T>(u[j]);
-    __syncwarp();
-    {
-      S a = buf[iz[0]], bq = buf[iz[1]], c = buf[iz[2]], d = buf[iz[3]];
-      lift_inv(a, bq, c, d);
-      buf[iz[0]] = a; buf[iz[1]] = bq; buf[iz[2]] = c; buf[iz[3]] = d;
+      for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
+      __syncwarp();
+      lift_inv(r[0], r[1], r[2], r[3]);
     }
-    __syncwarp();
-    {
-      S a = buf[iy[0]], bq = buf[iy[1]], c = buf[iy[2]], d = buf[iy[3]];
-      lift_inv(a, bq, c, d);
-      buf[iy[0]] = a; buf[iy[1]] = bq; buf[iy[2]] = c; buf[iy[3]] = d;
-    }
-    __syncwarp();
-    S r[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) r[m] = buf[ix[m]];
-    __syncwarp();
-    lift_inv(r[0], r[1], r[2], r[3]);
-    if (my.mode == kModeCoded) dequantize_line<T, true>(r, my.s, xi);
+    if (conv && my.mode == kModeCoded) dequantize_line<T, true>(r, my.s, xi);
   }
   if (my.mode == kModeRaw) {
 #pragma unroll
@@ -572,7 +637,7 @@ __device__ __forceinline__ void parse_round(const BoxJob& J, unsigned int* err, 
   }
 }
 
-template <typename T>
+template <typename T, bool SC>
 __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams R) {
   using F = Fmt<T>;
   using S = typename F::S;
@@ -645,7 +710,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
           const int L = jj * ub + uA;
           const BlockMeta mA = meta[L], mB = meta[L + 1];
           T xi[4];
-          rebuild_pair<T>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP, spill + (L + 1) * SP,
+          rebuild_pair<T, SC>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP, spill + (L + 1) * SP,
                           &J.comp[J.k0 + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
           for (int m = 0; m < 4; ++m) xt[m] = F::add(xt[m], xi[m]);  // x~ += x_j
@@ -675,7 +740,7 @@ __global__ void __launch_bounds__(kRThreads, 3) k_retrieve3(const RetrieveParams
             const int L = jj * 32 + uA;
             const BlockMeta mA = meta[L], mB = meta[L + 1];
             T xi[4];
-            rebuild_pair<T>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP,
+            rebuild_pair<T, SC>(mA, mB, slots + L * Slots<T>::n, slots + (L + 1) * Slots<T>::n, spill + L * SP,
                             spill + (L + 1) * SP, &J.comp[base + jj], buf, ix, iy, iz, ir, tkeep, lane, h, t, xi);
 #pragma unroll
             for (int m = 0; m < 4; ++m) xt[q][m] = F::add(xt[q][m], xi[m]);
@@ -711,8 +776,8 @@ static int retrieve_grid_t(int64_t nunits) {
     int dev = 0, sms = 0, ps = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_retrieve3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)retrieve_smem3<T>());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_retrieve3<T>, kRThreads, retrieve_smem3<T>()) !=
+    cudaFuncSetAttribute(k_retrieve3<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)retrieve_smem3<T>());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_retrieve3<T, false>, kRThreads, retrieve_smem3<T>()) !=
         cudaSuccess) {
       cudaGetLastError();
       ps = 1;
@@ -732,13 +797,30 @@ size_t retrieve_spill_words(int dtype, int ndims, int grid) {
   return (dtype == 1 ? spill_words_per_cta<float>() : spill_words_per_cta<double>()) * (size_t)grid;
 }
 
+// Float64 retrieval decoding at least this many components per brick takes
+// the kernel with the 32-bit decoding of narrow pairs (SC): measured 7.5 %
+// faster over k = 1..8 of a 512^3 field with 8 components, but 8 % slower at
+// k = 1 and even at k = 2, where the parse, whose registers the extra path
+// crowds, dominates.  Lists of jobs (batches, served queries) take it too.
+constexpr int kScaledMinComponents = 3;
+
 template <typename T>
 static cudaError_t launch_retrieve_t(const RetrieveParams& p, cudaStream_t s) {
   const size_t smem = retrieve_smem3<T>();
-  cudaError_t e = cudaFuncSetAttribute(k_retrieve3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_retrieve3<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if constexpr (sizeof(T) == 8)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_retrieve3<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (p.nunits == 0) return cudaSuccess;
-  k_retrieve3<T><<<(unsigned)p.grid, kRThreads, smem, s>>>(p);
+  bool sc = false;
+  if constexpr (sizeof(T) == 8) sc = p.jobs != nullptr || p.job0.k - p.job0.k0 >= kScaledMinComponents;
+  if constexpr (sizeof(T) == 8)
+    if (sc) {
+      k_retrieve3<T, true><<<(unsigned)p.grid, kRThreads, smem, s>>>(p);
+      return cudaGetLastError();
+    }
+  k_retrieve3<T, false><<<(unsigned)p.grid, kRThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
