@@ -53,16 +53,18 @@ N_COMP = 8
 METRIC = "compress/retrieve GB/s vs HBM roofline; progressive-query p50/p99 latency"
 # DRAM bytes (read + write) and warp instructions per launch of the dominant kernel on this
 # workload, means over the 16 retrieval launches of a step (k = 1..8, float32 and float64), from
-# one ncu capture of the current kernels at 512^3 (gpu__time_duration, dram__bytes_read/write,
-# smsp__inst_executed: one pass).
-TRAFFIC = {"retrieve": 1291889936}
+# ncu captures of the current kernels at 512^3 (gpu__time_duration, dram__bytes_read/write,
+# smsp__inst_executed: one pass), one per type.
+TRAFFIC = {"retrieve": 1298626048}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over the 16 retrieval launches "
                   "(k = 1..8, float32 and float64) of this workload at 512^3")
-INSTRUCTIONS = {"retrieve": 2051047084}
+INSTRUCTIONS = {"retrieve": 2046510995}
 # Pipe utilisation (ncu --set full on the 320^3 case of this workload): the retrieval (k = 8)
-# and compression kernels are bound by instruction issue, not by HBM.  The retrieval figures
-# are of the current kernel; compression has since dropped a warp vote and some FP64
-# operations (2-4 % less time), its figures are of the kernel before that.
+# and compression kernels are bound by instruction issue, not by HBM.  The float32 retrieval
+# figures are of the current kernel; the float64 ones of the kernel before the 32-bit decoding
+# of narrow brick pairs (11 % less time at k = 8 since, with the int -> double conversions off
+# the FP64 pipe); compression has since dropped a warp vote and some FP64 operations (2-4 %
+# less time), its figures are of the kernel before that.
 PIPES = {"launch": "320^3, retrieval at k = 8, compression of 8 components",
          "retrieve": {"alu": {"f32": 0.569, "f64": 0.574}, "fp64": {"f32": 0.0, "f64": 0.662},
                       "issue_active": {"f32": 0.677, "f64": 0.604}},
@@ -70,7 +72,8 @@ PIPES = {"launch": "320^3, retrieval at k = 8, compression of 8 components",
                       "issue_active": {"f32": 0.762, "f64": 0.584}},
          "source": "ncu sm__inst_executed_pipe_{alu,fp64}.avg.pct_of_peak_sustained_active, "
                    "smsp__issue_active.avg.pct_of_peak_sustained_active; compression figures from the "
-                   "kernel before its last change (2-4 % less time since)"}
+                   "kernel before its last change (2-4 % less time since); float64 retrieval figures from the "
+                   "kernel before its 32-bit decoding of narrow brick pairs (11 % less time at k = 8 since)"}
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
                   "384x384x256 (not multiples of 4), half sums of Gaussians and half k^-5/3 spectra, 6 components "
                   "(tau_i = 1e-(i+1) * range)")
