@@ -799,9 +799,10 @@ size_t retrieve_spill_words(int dtype, int ndims, int grid) {
 
 // Float64 retrieval decoding at least this many components per brick takes
 // the kernel with the 32-bit decoding of narrow pairs (SC): measured 7.5 %
-// faster over k = 1..8 of a 512^3 field with 8 components, but 8 % slower at
-// k = 1 and even at k = 2, where the parse, whose registers the extra path
-// crowds, dominates.  Lists of jobs (batches, served queries) take it too.
+// faster over k = 1..8 of a 512^3 field with 8 components (11 % at k = 8), but
+// 8 % slower at k = 1 and 1 % slower at k = 2, where the parse, whose
+// registers the extra path crowds, dominates.  Lists of jobs (batches, served
+// queries) take it too.
 constexpr int kScaledMinComponents = 3;
 
 template <typename T>
