@@ -617,7 +617,11 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       if (line_in && m < nvx) {
-        const U a = F::bits(e[m]) & F::ABS;
+        U a;  // float64: |e|'s pattern doubled (mag2_bits), halved after the maximum
+        if constexpr (sizeof(U) == 8)
+          a = mag2_bits(e[m]);
+        else
+          a = F::bits(e[m]) & F::ABS;
         merr = a > merr ? a : merr;
       }
     }
@@ -628,7 +632,7 @@ __device__ __forceinline__ void compress3_chunk(const CompressParams& P, int64_t
     } else {  // per brick half: the two halves' 64-bit maxima, four warp reductions
       const unsigned long long lo = warp_max_u64(FULL, h ? 0ull : (unsigned long long)merr);
       const unsigned long long hi = warp_max_u64(FULL, h ? (unsigned long long)merr : 0ull);
-      merr = (U)(h ? hi : lo);
+      merr = (U)(h ? hi : lo) >> 1;
     }
     // failures are counted only where a brick of the warp is RAW (a CODED or
     // ZERO brick meets tau_i on every value by construction)

@@ -305,7 +305,11 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
       if (have && (k & 3) < nvx && (k >> 2) < nvy) {
         const T r = F::sub(x[k], xt[k]);
         if (!within<T>(r, tb)) ++viol;
-        const unsigned long long a = (unsigned long long)(F::bits(r) & F::ABS);
+        unsigned long long a;  // float64: |r|'s pattern doubled (mag2_bits), halved after the maximum
+        if constexpr (sizeof(T) == 8)
+          a = mag2_bits(r);
+        else
+          a = (unsigned long long)(F::bits(r) & F::ABS);
         merr = a > merr ? a : merr;
       }
     }
@@ -316,7 +320,7 @@ __device__ __forceinline__ void compress_small_chunk(const CompressParams& P, in
     if constexpr (sizeof(T) == 4)  // 32-bit patterns: one warp reduction (redux)
       merr = __reduce_max_sync(FULL, (unsigned)merr);
     else
-      merr = warp_max_u64(FULL, merr);
+      merr = warp_max_u64(FULL, merr) >> 1;
     // escalations and Eq. 1 failures (RAW bricks only) are rare: summed only
     // where a lane has some
     if (__any_sync(FULL, se != 0 || viol != 0)) {
