@@ -64,7 +64,8 @@ INSTRUCTIONS = {"retrieve": 2046510995}
 # figures are of the current kernel; the float64 ones of the kernel before the 32-bit decoding
 # of narrow brick pairs (11 % less time at k = 8 since, with the int -> double conversions off
 # the FP64 pipe); compression has since dropped a warp vote and some FP64 operations (2-4 %
-# less time), its figures are of the kernel before that.
+# less time; float64 9 %, its magnitude tests no longer compiling to FP64 adds), its figures
+# are of the kernel before that.
 PIPES = {"launch": "320^3, retrieval at k = 8, compression of 8 components",
          "retrieve": {"alu": {"f32": 0.569, "f64": 0.574}, "fp64": {"f32": 0.0, "f64": 0.662},
                       "issue_active": {"f32": 0.677, "f64": 0.604}},
@@ -72,7 +73,8 @@ PIPES = {"launch": "320^3, retrieval at k = 8, compression of 8 components",
                       "issue_active": {"f32": 0.762, "f64": 0.584}},
          "source": "ncu sm__inst_executed_pipe_{alu,fp64}.avg.pct_of_peak_sustained_active, "
                    "smsp__issue_active.avg.pct_of_peak_sustained_active; compression figures from the "
-                   "kernel before its last change (2-4 % less time since); float64 retrieval figures from the "
+                   "kernel before its last changes (2-4 % less time since for float32, 9 % for float64, whose "
+                   "magnitude tests no longer compile to FP64 adds); float64 retrieval figures from the "
                    "kernel before its 32-bit decoding of narrow brick pairs (11 % less time at k = 8 since)"}
 BATCH_WORKLOAD = ("64 float32 fields, half 2D with extents in [256, 4096], half 3D between 32^3 and "
                   "384x384x256 (not multiples of 4), half sums of Gaussians and half k^-5/3 spectra, 6 components "
