@@ -166,7 +166,6 @@ __global__ void __launch_bounds__(kTileX * kTileY) k_vorticity_z4(const float* _
   const int x4 = (blockIdx.x * kTileX + lane) * 4;
   const bool act = x4 < nx && y < ny;  // every lane stays for the shuffles
   const int z0 = blockIdx.z * zchunk, z1 = min(nz, z0 + zchunk);
-  const int64_t plane = (int64_t)nx * ny;
   // rows of the y-derivative: (y + 1, y - 1) inside; the three-point ends otherwise
   const int ya = y == 0 ? 1 : y == ny - 1 ? ny - 1 : y + 1;
   const int yb = y == 0 ? 0 : y == ny - 1 ? ny - 2 : y - 1;
